@@ -1,0 +1,253 @@
+"""Pins of the oracle's cycles (Alg. 1, Alg. 2, Eq. 2, Eq. 4, Eq. 9, Eq. 10)."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spl
+
+import workloads as wl
+from oracle import cycle, fem, transfer
+from tests import _brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "smoothed_prolongation_2d.txt")
+
+
+def _golden():
+    return np.loadtxt(GOLDEN, comments="#")
+
+
+def test_smoothed_stencil_matches_the_printed_one():
+    # Sec. 3.2 prints M^{-1} A_{eps=1} P (d = 2) to three or four digits
+    S = cycle.smoothed_prolongation_stencil(2)
+    G = _golden()
+    assert G.shape == (7, 7)
+    for v, g in zip(S.ravel(), G.ravel()):
+        text = f"{g:.10g}"
+        digits = len(text.split(".")[1]) if "." in text else 0
+        assert abs(v - g) <= 0.6 * 10.0 ** (-max(digits, 3)) + 1e-12, (v, g)
+
+
+def test_truncated_stencil_facts_2d():
+    S = cycle.smoothed_prolongation_stencil(2)
+    T = cycle.truncate_stencil(S)
+    ring = S.copy()
+    ring[1:6, 1:6] = 0.0
+    assert ring.max() <= 1e-15                       # dropped entries are <= 0
+    assert T.min() >= -1e-15
+    nz = np.argwhere(np.abs(T) > 1e-14)
+    assert len(nz) == 9                              # a plus: centre, +-1, +-2
+    assert all((i == 2) or (j == 2) for i, j in nz)
+    assert T[2, 2] == pytest.approx(4 / 9)
+    assert T[2, 1] == pytest.approx(1 / 6) and T[0, 2] == pytest.approx(1 / 12)
+    assert T.sum() == pytest.approx(13 / 9)
+
+
+def test_truncated_stencil_facts_3d():
+    S = cycle.smoothed_prolongation_stencil(3)
+    T = cycle.truncate_stencil(S)
+    ring = S.copy()
+    ring[1:6, 1:6, 1:6] = 0.0
+    assert ring.max() <= 1e-15
+    assert T.min() >= -1e-15
+    assert int(np.sum(np.abs(T) > 1e-14)) == 61
+    assert T[2, 2, 2] == pytest.approx(16 / 27)
+    assert T.sum() == pytest.approx(169 / 27)
+    # full smoothed operator: zero sum (A annihilates constants away from the
+    # boundary), symmetric under axis permutations and reflections
+    assert abs(S.sum()) < 1e-13
+    np.testing.assert_allclose(S, S.transpose(1, 0, 2), atol=1e-15)
+    np.testing.assert_allclose(S, S[::-1], atol=1e-15)
+
+
+@pytest.mark.parametrize("d,variant", [(2, "jac"), (2, "additive"), (2, "pi"), (3, "jac")])
+def test_single_level_is_damped_jacobi(d, variant):
+    # L = l_min = 1: no coarser level, the cycle is one damped Jacobi step;
+    # diag(A) = 8 eps / 3 (2-D) or 32 h eps / 12 (3-D) for constant eps
+    eps = 2.0
+    n = 3
+    f = np.random.default_rng(0).standard_normal((n + 1,) * d)
+    H = cycle.build_hierarchy(d, 1, [eps], True, f)
+    u = fem.zero_boundary(np.random.default_rng(1).standard_normal((n + 1,) * d))
+    got = cycle.cycle(H, u, variant=variant)
+    dg = 8 * eps / 3 if d == 2 else 32 * eps / (12 * n)
+    want = u + 0.6 * (H.b - H.fine.op.apply(u)) / dg
+    fem.zero_boundary(want)
+    np.testing.assert_allclose(got, want, atol=1e-14)
+
+
+def _dense_hierarchy(d, L, eps):
+    """A_l, P_l, D_l as dense interior matrices, from global hats and quadrature."""
+    A = {}
+    Pm = {}
+    n = 3 ** L
+    Afull = _brute.stiffness_dense(d, n, eps)
+    fin = _brute.interior_mask(d, n)
+    A[L] = Afull[np.ix_(fin, fin)]
+    for l in range(L, 1, -1):
+        n_c = 3 ** (l - 1)
+        Pd = _brute.dlinear_prolongation_dense(d, n_c)
+        Pm[l] = Pd[np.ix_(_brute.interior_mask(d, 3 * n_c), _brute.interior_mask(d, n_c))]
+        A[l - 1] = Pm[l].T @ A[l] @ Pm[l]
+    D = {l: np.diag(np.diag(A[l])) for l in A}
+    return A, Pm, D
+
+
+def _injection_dense(d, n_c):
+    n_f = 3 * n_c
+    cin = [J for J in itertools.product(range(1, n_c), repeat=d)]
+    fin = [i for i in itertools.product(range(1, n_f), repeat=d)]
+    fpos = {i: k for k, i in enumerate(fin)}
+    I = np.zeros((len(cin), len(fin)))
+    for k, J in enumerate(cin):
+        I[k, fpos[tuple(3 * j for j in J)]] = 1.0
+    return I
+
+
+def _rtilde_truncated_2d_dense(n_c):
+    """R~ from the closed-form entries of the printed stencil's 5x5 core:
+    4/9 at the coarse vertex, 1/6 and 1/12 at distance 1 and 2 along the axes."""
+    n_f = 3 * n_c
+    cin = [J for J in itertools.product(range(1, n_c), repeat=2)]
+    fin = [i for i in itertools.product(range(1, n_f), repeat=2)]
+    fpos = {i: k for k, i in enumerate(fin)}
+    w = {0: 4 / 9, 1: 1 / 6, 2: 1 / 12}
+    Rt = np.zeros((len(cin), len(fin)))
+    for k, J in enumerate(cin):
+        c = (3 * J[0], 3 * J[1])
+        for t in range(-2, 3):
+            for p in ((c[0] + t, c[1]), (c[0], c[1] + t)):
+                if p in fpos:
+                    Rt[k, fpos[p]] = w[abs(t)]
+    return Rt
+
+
+@pytest.mark.parametrize("d,L,variant,rtilde", [
+    (2, 2, "jac", "truncated"), (2, 3, "jac", "truncated"), (2, 3, "jac", "exact"),
+    (2, 3, "additive", "truncated"), (2, 3, "pi", "truncated"), (2, 3, "exp", "truncated"),
+    (3, 2, "jac", "exact"), (3, 2, "pi", "exact")])
+def test_cycle_equals_dense_restatement_of_eq9(d, L, variant, rtilde):
+    rng = np.random.default_rng(12)
+    n = 3 ** L
+    eps = rng.uniform(0.2, 3.0, size=(n,) * d)
+    f = rng.standard_normal((n + 1,) * d)
+    H = cycle.build_hierarchy(d, L, eps, False, f)
+    u = fem.zero_boundary(rng.standard_normal((n + 1,) * d))
+    got = fem.interior(cycle.cycle(H, u, variant=variant, rtilde=rtilde, omega_exp=0.7)).ravel()
+
+    A, Pm, D = _dense_hierarchy(d, L, eps)
+    w = wt = 0.6
+    b = fem.interior(H.b).ravel()
+    ui = fem.interior(u).ravel()
+    r = b - A[L] @ ui
+
+    def Pchain(l):          # prolongation from level l to L
+        M = np.eye(A[L].shape[0])
+        for m in range(L, l, -1):
+            M = M @ Pm[m]
+        return M
+
+    M = np.zeros((A[L].shape[0], A[L].shape[0]))
+    for l in range(1, L + 1):
+        scale = 0.7 ** (L - l) if variant == "exp" else 1.0
+        M += scale * Pchain(l) @ (w * np.linalg.inv(D[l])) @ Pchain(l).T
+    if variant == "jac":
+        for l in range(2, L + 1):
+            if rtilde == "exact":
+                Rt = w * Pm[l].T @ A[l] @ np.linalg.inv(D[l])
+            else:
+                Rt = w * _rtilde_truncated_2d_dense(3 ** (l - 1))
+            M -= Pchain(l - 1) @ (wt * np.linalg.inv(D[l - 1])) @ Rt @ Pchain(l).T
+    if variant == "pi":
+        for l in range(2, L + 1):
+            PI = Pm[l] @ _injection_dense(d, 3 ** (l - 1))
+            M -= Pchain(l) @ PI @ (w * np.linalg.inv(D[l])) @ Pchain(l).T
+    want = ui + M @ r
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("transfer_kind", ["dlinear", "boxmg"])
+def test_fas_form_equals_correction_scheme(transfer_kind):
+    # with Galerkin operators, b_l - A_l I u = R r_{l+1} exactly (Eq. 4)
+    w = wl.get("jump2d_d6").with_depth(4)
+    eps, sc = w.eps()
+    H = cycle.build_hierarchy(2, 4, eps, sc, w.f(), transfer_kind)
+    u = wl.random_vertex_field(2, 4, 7)
+    for variant in ("jac", "pi", "additive"):
+        a = cycle.cycle(H, u, variant=variant, form="cs")
+        b = cycle.cycle(H, u, variant=variant, form="fas")
+        np.testing.assert_allclose(a, b, atol=1e-12 * np.abs(a).max())
+
+
+@pytest.mark.parametrize("d,L,transfer_kind", [(2, 3, "boxmg"), (2, 3, "dlinear"), (3, 2, "boxmg")])
+def test_all_variants_converge_to_the_direct_solution(d, L, transfer_kind):
+    rng = np.random.default_rng(21)
+    n = 3 ** L
+    eps = rng.choice([1.0, 1e-2], size=(n,) * d)
+    f = np.ones((n + 1,) * d)
+    H = cycle.build_hierarchy(d, L, eps, False, f, transfer_kind)
+    Afull = _brute.stiffness_dense(d, n, eps)
+    fin = _brute.interior_mask(d, n)
+    x = np.linalg.solve(Afull[np.ix_(fin, fin)], fem.interior(H.b).ravel())
+    for variant in ("jac", "pi", "additive"):
+        u, hist = cycle.solve(H, variant=variant, tol=1e-13, max_cycles=2000)
+        assert hist[-1] <= 1e-13
+        np.testing.assert_allclose(fem.interior(u).ravel(), x, rtol=1e-9,
+                                   atol=1e-10 * np.abs(x).max())
+
+
+def test_manufactured_solution_error_is_second_order():
+    errs = {}
+    for d, depths in ((2, (3, 4, 5)), (3, (2, 3))):
+        for L in depths:
+            w = wl.Workload("m", d, L, "scalar")
+            H = cycle.build_hierarchy(d, L, *w.eps(), w.f())
+            u, hist = cycle.solve(H, tol=1e-10, max_cycles=400)
+            errs[d, L] = np.abs(u - wl.manufactured_solution(d, L)).max()
+    for d, L in ((2, 3), (2, 4), (3, 2)):
+        ratio = errs[d, L] / errs[d, L + 1]
+        assert 8.0 < ratio < 10.0, (d, L, ratio)
+
+
+def test_residual_norm_eq10():
+    H = cycle.build_hierarchy(2, 2, [1.0], True, np.zeros((10, 10)))
+    r = np.zeros((10, 10))
+    r[1:-1, 1:-1] = 2.0
+    assert cycle.residual_norm(H, r) == pytest.approx(np.sqrt(64 * 4 / 81))
+    assert cycle.max_residual(r) == 2.0
+
+
+def _lambda_max(H, variant):
+    L, d = H.L, H.d
+    n = 3 ** L
+    N = (n - 1) ** d
+    I = tuple(slice(1, -1) for _ in range(d))
+    b_saved = H.b.copy()
+    H.b[:] = 0.0
+
+    def BA(x):
+        u = np.zeros((n + 1,) * d)
+        u[I] = x.reshape((n - 1,) * d)
+        return (u - cycle.cycle(H, u, variant=variant))[I].ravel()
+
+    op = spl.LinearOperator((N, N), matvec=BA)
+    lam = spl.eigs(op, k=1, which="LM", return_eigenvectors=False, maxiter=5000)
+    H.b[:] = b_saved
+    return float(np.abs(lam).max())
+
+
+def test_plain_additive_overshoot_grows_with_the_number_of_levels():
+    # Sec. 2.2 / 5.1: summing all levels' corrections overshoots more the more
+    # levels there are (lambda_max of the preconditioned operator B A grows
+    # towards 2, where the iteration stops converging); adAFAC's damping keeps
+    # lambda_max lower, adAFAC-PI keeps it below one
+    lam = {}
+    for L in (2, 3, 4):
+        H = cycle.build_hierarchy(2, L, [1.0], True, np.zeros((3 ** L + 1,) * 2))
+        for v in ("additive", "jac", "pi"):
+            lam[v, L] = _lambda_max(H, v)
+    assert lam["additive", 2] < lam["additive", 3] < lam["additive", 4]
+    assert lam["additive", 4] > 1.5
+    for L in (3, 4):
+        assert lam["jac", L] < lam["additive", L] - 0.2
+        assert lam["pi", L] < 1.0
