@@ -1,0 +1,207 @@
+/*
+ * adafac.h -- C ABI of the GB300 adAFAC multigrid library.
+ *
+ * The library solves the vertex-based d-linear finite element discretisation
+ * of  -div(eps grad u) = f  (Eq. 1 of Murray & Weinzierl, "Stabilised
+ * Asynchronous Fast Adaptive Composite Multigrid using Additive Damping",
+ * arXiv:1903.10367) on the unit square/cube with zero Dirichlet data, on a
+ * regular spacetree of depth L with 3:1 refinement per dimension (Sec. 2.1).
+ * Levels are numbered l = 1 (coarsest level with unknowns, l_min) .. L
+ * (finest, l_max); level l has n_l = 3^l cells per dimension and
+ * (n_l + 1)^d vertices, of which (n_l - 1)^d interior ones are unknowns.
+ *
+ * One call of adafac_cycle() runs additive multigrid cycles in which every
+ * level at once computes its residual, one damped Jacobi step and (adAFAC-Jac)
+ * the auxiliary damping equation on the next coarser level; all corrections
+ * are prolonged and summed (Algorithm 1, Eq. 9).  Everything after the input
+ * copy runs in the library's CUDA kernels on the caller's stream.
+ *
+ * Array layout (all vertex arrays): C order, x fastest, then y, then z; an
+ * array of a level with n cells holds (n+1)^d entries including the boundary
+ * ring.  Per-cell arrays hold n^d entries in the same order.
+ *
+ * Conventions of every entry point:
+ *   - returns an adafac_status; never aborts, never throws;
+ *   - a failing call leaves a message retrievable with adafac_last_error();
+ *   - calls on one handle are not thread-safe; different handles are
+ *     independent;
+ *   - device work is enqueued on the handle's stream; functions documented
+ *     as "synchronises" wait for that stream.
+ */
+#ifndef ADAFAC_H
+#define ADAFAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adafac_handle_s* adafac_handle;
+
+typedef enum {
+  ADAFAC_OK = 0,
+  ADAFAC_ERR_INVALID_ARG = 1,   /* bad pointer, size, option or state       */
+  ADAFAC_ERR_OOM = 2,           /* workspace too small / allocation failed  */
+  ADAFAC_ERR_DIVERGED = 3,      /* residual non-finite or grew > 1e6 x r_0  */
+  ADAFAC_ERR_TIMEOUT = 4,       /* reserved for bounded device waits        */
+  ADAFAC_ERR_CUDA = 5,          /* a CUDA runtime call failed               */
+  ADAFAC_ERR_NOT_CONVERGED = 6  /* adafac_solve hit max_cycles              */
+} adafac_status;
+
+/* Regular spacetree: dim in {2, 3}, 1 <= depth (L), ((3^L+1)^dim must fit in
+ * 2^31 vertices).  l_min is fixed to 1 (the paper's benchmark setting,
+ * Sec. 2.1). */
+typedef struct {
+  int dim;
+  int depth;
+} adafac_tree;
+
+enum {
+  ADAFAC_VARIANT_ADDITIVE = 0,  /* plain additive multigrid, Eq. 2          */
+  ADAFAC_VARIANT_JAC = 1,       /* adAFAC-Jac, Algorithm 1 / Eq. 9          */
+  ADAFAC_VARIANT_PI = 2,        /* adAFAC-PI, Algorithm 2                   */
+  ADAFAC_VARIANT_EXP = 3        /* Eq. 2 with omega_add(l) = omega_exp^(L-l) */
+};
+enum { ADAFAC_TRANSFER_DLINEAR = 0, ADAFAC_TRANSFER_BOXMG = 1 };
+enum { ADAFAC_PRECISION_FP64 = 0, ADAFAC_PRECISION_MIXED = 1 };
+enum { ADAFAC_RTILDE_TRUNCATED = 0, ADAFAC_RTILDE_EXACT = 1 };
+enum { ADAFAC_FORM_CS = 0, ADAFAC_FORM_FAS = 1 };
+
+typedef struct {
+  int variant;        /* ADAFAC_VARIANT_*, default JAC                        */
+  int transfer;       /* ADAFAC_TRANSFER_*: d-linear or BoxMG (Sec. 2.4)      */
+  int precision;      /* FP64: every step in FP64.  MIXED: the cycles run in
+                         FP32 on the correction equation A e = r, grouped into
+                         refinement steps whose residual r = b - A u and update
+                         u += e are FP64 (iterative refinement).              */
+  int rtilde;         /* smoothed restriction R~ (Sec. 3.2, option 1):
+                         TRUNCATED = omega (M^-1 A_{eps=1} P)^T cut to the 5^d
+                         support of P; EXACT = omega R A_l M_l^-1             */
+  int form;           /* CS: coarse residuals r_l = R r_{l+1};  FAS: injected
+                         coarse solutions and FAS/HTMG right-hand sides
+                         (Eq. 4).  FAS requires precision FP64.               */
+  int inner_cycles;   /* MIXED: FP32 cycles per FP64 refinement step (>= 1)  */
+  double omega;       /* Jacobi damping, default 0.6 (Sec. 5)                */
+  double omega_tilde; /* damping-equation Jacobi damping, default 0.6        */
+  double omega_exp;   /* base of exponential damping (VARIANT_EXP)           */
+} adafac_options;
+
+/* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,
+ * inner_cycles 12, omega = omega_tilde = 0.6, omega_exp = 0.5. */
+adafac_status adafac_default_options(adafac_options* opt);
+
+/* Device bytes a handle for (tree, opt) needs.  Pass at least this much
+ * 256-byte aligned device memory to adafac_setup, or NULL there to let the
+ * library allocate it. */
+adafac_status adafac_workspace_size(const adafac_tree* tree,
+                                    const adafac_options* opt, size_t* bytes);
+
+/* Builds the hierarchy (Sec. 2.1-2.4): load vector b_L = h^d f (lumped mass),
+ * fine operator from per-cell eps, for l = L..2 the prolongation P_l
+ * (d-linear or BoxMG) and the Galerkin operator A_{l-1} = P_l^T A_l P_l, the
+ * inverse diagonals, and the smoothed-restriction stencil.  All in FP64; MIXED
+ * keeps FP32 copies for the cycles.  The iterate starts at u = 0.
+ *
+ *   eps   per finest-level cell (3^L)^dim doubles, or one double if
+ *         eps_is_scalar; every value must be > 0
+ *   f     right-hand side at every finest-level vertex, (3^L+1)^dim doubles
+ *         (boundary entries ignored), or NULL for f = 0
+ *   inputs_on_device  0: eps and f are host pointers (copied, may be pageable);
+ *                     1: device pointers (copied device-to-device)
+ *   workspace / workspace_bytes  caller-owned device memory of at least
+ *         adafac_workspace_size() bytes that outlives the handle, or NULL
+ *         (library allocates and frees it)
+ *   stream  cudaStream_t for all device work of this handle (NULL: default)
+ *
+ * Inputs are copied; the caller may free them once the call returns.
+ * Synchronises.  On failure *out is NULL and nothing stays allocated. */
+adafac_status adafac_setup(const adafac_tree* tree, const double* eps,
+                           int eps_is_scalar, const double* f,
+                           int inputs_on_device, const adafac_options* opt,
+                           void* workspace, size_t workspace_bytes,
+                           void* stream, adafac_handle* out);
+
+/* Enqueues n_cycles >= 0 cycles (Algorithm 1 / Eq. 9 or the chosen variant).
+ * FP64: each cycle updates u.  MIXED: the cycles act on the FP32 correction
+ * equation in groups of at most inner_cycles; each group starts from the FP64
+ * residual of u and ends with u += e, so u is current when the call returns.
+ * Asynchronous. */
+adafac_status adafac_cycle(adafac_handle h, int n_cycles);
+
+/* Runs cycles until ||r||_h / ||r_0||_h <= rel_tol (Eq. 10, r_0 = b for the
+ * initial u = 0 of setup, or the residual at the last adafac_set_solution /
+ * adafac_reset) or max_cycles cycles.  The test runs on the device; batches of
+ * cycles after convergence return immediately.  *cycles_done receives the
+ * number of cycles applied, *rel the final normalised residual (either may be
+ * NULL).  Returns ADAFAC_ERR_NOT_CONVERGED or ADAFAC_ERR_DIVERGED when the
+ * tolerance was not met.  Synchronises. */
+adafac_status adafac_solve(adafac_handle h, double rel_tol, int max_cycles,
+                           int* cycles_done, double* rel);
+
+/* Residual of the current iterate in FP64: *abs = ||b - A u||_h (Eq. 10)
+ * and *rel = *abs / ||r_0||_h.  Either pointer may be NULL.  Synchronises. */
+adafac_status adafac_residual_norm(adafac_handle h, double* rel, double* abs);
+
+/* Copies the current fine-level iterate u ((3^L+1)^dim doubles including the
+ * zero boundary) to dst (host if dst_on_device == 0, else device).
+ * Synchronises. */
+adafac_status adafac_solution(adafac_handle h, double* dst, int dst_on_device);
+
+/* Sets the iterate u from src (same layout; boundary entries are ignored and
+ * kept zero) and makes its residual the new r_0.  Synchronises. */
+adafac_status adafac_set_solution(adafac_handle h, const double* src,
+                                  int src_on_device);
+
+/* Resets u = 0 and r_0 = b.  Asynchronous. */
+adafac_status adafac_reset(adafac_handle h);
+
+/* Inspection of internal per-level arrays (for tests and diagnostics).
+ * field: ADAFAC_FIELD_*; level: 1..L.  Copies the array as doubles to dst
+ * (host or device) and writes its length to *count (pass dst = NULL to query
+ * the length only).  Vectors have (n_l+1)^d entries; P has 2^d entries per
+ * vertex of level l (entry c weights the corner with offset bit j = (c>>j)&1
+ * along dimension j, x = 0, of the owning coarse cell
+ * floor(min(i/3, n_{l-1}-1))), stored entry-major (c * V + vertex);
+ * STENCIL has 3^d entries per vertex, entry s = sum_j (o_j+1) 3^j, stored
+ * entry-major.  Vectors of the most recent cycle: R residual r_l, BT damping
+ * right-hand side b~_l, G combined correction g_l = c_l - c~_l, T prolonged
+ * sum t_l.  Synchronises. */
+enum {
+  ADAFAC_FIELD_U = 0,       /* fine iterate (level L only)                 */
+  ADAFAC_FIELD_B = 1,       /* fine load vector (level L only)             */
+  ADAFAC_FIELD_R = 2,
+  ADAFAC_FIELD_BT = 3,
+  ADAFAC_FIELD_G = 4,
+  ADAFAC_FIELD_T = 5,
+  ADAFAC_FIELD_P = 6,       /* prolongation l-1 -> l (l >= 2, BoxMG only)  */
+  ADAFAC_FIELD_STENCIL = 7, /* Galerkin stencil of level l < L             */
+  ADAFAC_FIELD_INVDIAG = 8  /* 1 / diag(A_l)                               */
+};
+adafac_status adafac_get_field(adafac_handle h, int field, int level,
+                               double* dst, int dst_on_device, size_t* count);
+
+/* Normalised residual history: entry k is ||r_k||_h / ||r_0||_h of the k-th
+ * residual evaluated on the device since setup/reset (one per FP64 cycle,
+ * one per refinement step in MIXED).  Copies up to max_entries doubles to the
+ * host array dst and the number available to *count.  Synchronises. */
+adafac_status adafac_history(adafac_handle h, double* dst, int max_entries,
+                             int* count);
+
+/* Number of kernel launches the library has enqueued on this handle since
+ * setup (setup kernels excluded). */
+adafac_status adafac_launch_count(adafac_handle h, uint64_t* count);
+
+/* Message of the last failing call on h (or of the last failing setup when
+ * h is NULL).  The pointer stays valid until the next call on h. */
+const char* adafac_last_error(adafac_handle h);
+
+/* Releases the handle and the workspace it allocated.  Synchronises. */
+adafac_status adafac_destroy(adafac_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADAFAC_H */

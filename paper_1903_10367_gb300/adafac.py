@@ -1,0 +1,256 @@
+"""Thin Python binding of the adAFAC C ABI (include/adafac.h).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+``libadafac.so``.  PyTorch provides the device workspace (a uint8 tensor) and
+the CUDA stream.  The binding raises ``AdafacError`` on every non-zero status
+and refuses to run without the compiled library: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "AdafacError", "Tree", "Options", "load", "default_options", "workspace_size",
+    "Solver", "FIELD", "VARIANT", "TRANSFER", "PRECISION", "RTILDE", "FORM",
+]
+
+VARIANT = {"additive": 0, "jac": 1, "pi": 2, "exp": 3}
+TRANSFER = {"dlinear": 0, "boxmg": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+RTILDE = {"truncated": 0, "exact": 1}
+FORM = {"cs": 0, "fas": 1}
+FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DIVERGED", 4: "TIMEOUT", 5: "CUDA",
+          6: "NOT_CONVERGED"}
+
+
+class AdafacError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"adafac {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Tree(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("depth", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("transfer", ctypes.c_int),
+                ("precision", ctypes.c_int), ("rtilde", ctypes.c_int),
+                ("form", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double),
+                ("omega_exp", ctypes.c_double)]
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every entry point declared in include/adafac.h
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGNATURES = [
+    ("adafac_default_options", _I, [ctypes.POINTER(Options)]),
+    ("adafac_workspace_size", _I, [ctypes.POINTER(Tree), ctypes.POINTER(Options),
+                                   ctypes.POINTER(ctypes.c_size_t)]),
+    ("adafac_setup", _I, [ctypes.POINTER(Tree), _P, _I, _P, _I, ctypes.POINTER(Options),
+                          _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    ("adafac_cycle", _I, [_P, _I]),
+    ("adafac_solve", _I, [_P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    ("adafac_residual_norm", _I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("adafac_solution", _I, [_P, _P, _I]),
+    ("adafac_set_solution", _I, [_P, _P, _I]),
+    ("adafac_reset", _I, [_P]),
+    ("adafac_get_field", _I, [_P, _I, _I, _P, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    ("adafac_history", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
+    ("adafac_launch_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    ("adafac_last_error", ctypes.c_char_p, [_P]),
+    ("adafac_destroy", _I, [_P]),
+]
+
+
+def load(build_if_missing: bool = True):
+    """Loads (building if needed) the shared library and declares its symbols."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise AdafacError(5, f"library not built: {path}")
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, handle=None):
+    if status != 0:
+        msg = _LIB.adafac_last_error(handle).decode(errors="replace")
+        raise AdafacError(status, msg)
+
+
+def default_options(**kw) -> Options:
+    lib = load()
+    o = Options()
+    _check(lib.adafac_default_options(ctypes.byref(o)))
+    for k, v in kw.items():
+        table = {"variant": VARIANT, "transfer": TRANSFER, "precision": PRECISION,
+                 "rtilde": RTILDE, "form": FORM}.get(k)
+        setattr(o, k, table[v] if table and isinstance(v, str) else v)
+    return o
+
+
+def workspace_size(dim: int, depth: int, opts: Options) -> int:
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib.adafac_workspace_size(ctypes.byref(Tree(dim, depth)), ctypes.byref(opts),
+                                     ctypes.byref(n)))
+    return n.value
+
+
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One adAFAC problem on the current CUDA device.
+
+    ``eps``: per-fine-cell array (shape (3^L,)*dim) or a scalar; ``f``: values
+    at every fine vertex (shape (3^L+1,)*dim) or None.  Host numpy arrays or
+    torch CUDA tensors (float64, contiguous) are accepted.
+    """
+
+    def __init__(self, dim: int, depth: int, eps, f=None, opts: Options | None = None,
+                 workspace=None, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.dim, self.depth = dim, depth
+        self.n = 3 ** depth
+        self.shape = (self.n + 1,) * dim
+        self.opts = opts if opts is not None else default_options()
+        eps_is_scalar = np.isscalar(eps) or (hasattr(eps, "numel") and eps.numel() == 1) or \
+            (isinstance(eps, np.ndarray) and eps.size == 1)
+        on_device = hasattr(eps, "is_cuda") and eps.is_cuda
+        keep = []
+        if on_device:
+            eps_t = eps.to(torch.float64).contiguous().reshape(-1)
+            f_t = None if f is None else f.to(torch.float64).contiguous()
+            keep += [eps_t, f_t]
+            eps_p = ctypes.c_void_p(eps_t.data_ptr())
+            f_p = None if f_t is None else ctypes.c_void_p(f_t.data_ptr())
+        else:
+            eps_a = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(-1))
+            f_a = None if f is None else np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+            if f_a is not None and f_a.shape != self.shape:
+                raise ValueError(f"f must have shape {self.shape}")
+            if not eps_is_scalar and eps_a.size != self.n ** dim:
+                raise ValueError(f"eps must have {self.n ** dim} entries")
+            keep += [eps_a, f_a]
+            eps_p = _host_ptr(eps_a)
+            f_p = None if f_a is None else _host_ptr(f_a)
+        nbytes = workspace_size(dim, depth, self.opts)
+        if workspace is None:
+            workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        self._ws = workspace
+        base = workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        avail = workspace.numel() - (aligned - base)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = ctypes.c_void_p()
+        _check(self.lib.adafac_setup(ctypes.byref(Tree(dim, depth)), eps_p, int(eps_is_scalar),
+                                     f_p, int(on_device), ctypes.byref(self.opts),
+                                     ctypes.c_void_p(aligned), avail,
+                                     ctypes.c_void_p(self.stream.cuda_stream),
+                                     ctypes.byref(self.h)))
+        del keep
+
+    # -- the C ABI, one method per entry point -----------------------------
+    def cycle(self, n: int = 1):
+        _check(self.lib.adafac_cycle(self.h, int(n)), self.h)
+
+    def solve(self, rel_tol: float = 1e-8, max_cycles: int = 1000, check: bool = True):
+        cycles = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = self.lib.adafac_solve(self.h, rel_tol, int(max_cycles), ctypes.byref(cycles),
+                                   ctypes.byref(rel))
+        if check:
+            _check(st, self.h)
+        return cycles.value, rel.value
+
+    def residual_norm(self):
+        rel = ctypes.c_double()
+        ab = ctypes.c_double()
+        _check(self.lib.adafac_residual_norm(self.h, ctypes.byref(rel), ctypes.byref(ab)), self.h)
+        return rel.value, ab.value
+
+    def solution(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        if isinstance(out, np.ndarray):
+            _check(self.lib.adafac_solution(self.h, _host_ptr(out), 0), self.h)
+        else:
+            _check(self.lib.adafac_solution(self.h, ctypes.c_void_p(out.data_ptr()), 1), self.h)
+        return out
+
+    def set_solution(self, u):
+        if isinstance(u, np.ndarray):
+            a = np.ascontiguousarray(u, dtype=np.float64)
+            _check(self.lib.adafac_set_solution(self.h, _host_ptr(a), 0), self.h)
+        else:
+            _check(self.lib.adafac_set_solution(self.h, ctypes.c_void_p(u.data_ptr()), 1), self.h)
+
+    def reset(self):
+        _check(self.lib.adafac_reset(self.h), self.h)
+
+    def field(self, name: str, level: int) -> np.ndarray:
+        count = ctypes.c_size_t()
+        _check(self.lib.adafac_get_field(self.h, FIELD[name], level, None, 0,
+                                         ctypes.byref(count)), self.h)
+        out = np.empty(count.value)
+        _check(self.lib.adafac_get_field(self.h, FIELD[name], level, _host_ptr(out), 0,
+                                         ctypes.byref(count)), self.h)
+        nl = 3 ** level
+        V = (nl + 1) ** self.dim
+        if out.size == V:
+            return out.reshape((nl + 1,) * self.dim)
+        return out.reshape((-1,) + (nl + 1,) * self.dim)
+
+    def history(self) -> np.ndarray:
+        count = ctypes.c_int()
+        _check(self.lib.adafac_history(self.h, None, 0, ctypes.byref(count)), self.h)
+        out = np.empty(max(count.value, 1))
+        _check(self.lib.adafac_history(self.h, _host_ptr(out), count.value,
+                                       ctypes.byref(count)), self.h)
+        return out[:count.value]
+
+    def launch_count(self) -> int:
+        c = ctypes.c_uint64()
+        _check(self.lib.adafac_launch_count(self.h, ctypes.byref(c)), self.h)
+        return c.value
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.adafac_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

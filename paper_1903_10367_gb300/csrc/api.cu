@@ -1,0 +1,878 @@
+// C ABI of the adAFAC library (declared in include/adafac.h): handle
+// lifetime, workspace layout, setup orchestration and the per-cycle launch
+// sequences.  Every numerical step runs in the kernels of setup.cu and
+// cycle.cu on the handle's stream.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/adafac.h"
+#include "engine.h"
+
+using namespace adafac;
+
+namespace {
+
+constexpr int kHistCap = 8192;
+constexpr int kNormBlocks = 152 * 8;
+
+thread_local std::string g_setup_error;
+
+struct LevelData {
+  int n = 0;
+  long long V = 0;
+  double *st = nullptr, *invd = nullptr, *P = nullptr, *Kc = nullptr;
+  double *r = nullptr, *bt = nullptr, *g = nullptr, *t = nullptr, *y = nullptr;
+  double *ul = nullptr, *bl = nullptr, *uhat = nullptr;
+  float *st32 = nullptr, *invd32 = nullptr, *P32 = nullptr;
+  float *r32 = nullptr, *bt32 = nullptr, *g32 = nullptr, *t32 = nullptr, *y32 = nullptr;
+  LevelView<double> v64;
+  LevelView<float> v32;
+};
+
+// Bump allocator over the workspace; with base == nullptr it only measures.
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(long long count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * (size_t)(count > 0 ? count : 0);
+    return p;
+  }
+};
+
+long long ipow_ll(long long b, int e) {
+  long long r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+}  // namespace
+
+struct adafac_handle_s {
+  int D = 0, L = 0;
+  adafac_options opt{};
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  bool uniform = false;    // scalar eps and d-linear: every level's stencil is uniform
+  int eps_scalar = 0;
+  double eps0 = 0.0;
+  LevelData lev[kMaxLevels + 1];
+  double *u = nullptr, *b = nullptr, *eps = nullptr;
+  float *eps32 = nullptr, *e32 = nullptr, *rhs32 = nullptr;
+  double* partials = nullptr;
+  Control* ctl = nullptr;
+  double* hist = nullptr;
+  CycleParams<double> cp64;
+  CycleParams<float> cp32;
+  std::string err;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+adafac_status fail(adafac_handle h, adafac_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_setup_error = msg;
+  return st;
+}
+
+adafac_status check_cuda(adafac_handle h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(h, ADAFAC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return ADAFAC_OK;
+}
+
+bool valid_options(const adafac_options* o, std::string* why) {
+  if (o->variant < 0 || o->variant > 3) return *why = "variant out of range", false;
+  if (o->transfer < 0 || o->transfer > 1) return *why = "transfer out of range", false;
+  if (o->precision < 0 || o->precision > 1) return *why = "precision out of range", false;
+  if (o->rtilde < 0 || o->rtilde > 1) return *why = "rtilde out of range", false;
+  if (o->form < 0 || o->form > 1) return *why = "form out of range", false;
+  if (o->form == ADAFAC_FORM_FAS && o->precision != ADAFAC_PRECISION_FP64)
+    return *why = "FAS form requires FP64 precision", false;
+  if (o->inner_cycles < 1) return *why = "inner_cycles must be >= 1", false;
+  if (!(o->omega > 0.0) || !(o->omega_tilde >= 0.0) || !(o->omega_exp > 0.0))
+    return *why = "damping factors must be positive", false;
+  return true;
+}
+
+bool valid_tree(const adafac_tree* t, std::string* why) {
+  if (t->dim != 2 && t->dim != 3) return *why = "dim must be 2 or 3", false;
+  if (t->depth < 1 || t->depth > kMaxLevels) return *why = "depth must be in 1..16", false;
+  const long long np1 = ipow_ll(3, t->depth) + 1;
+  if ((double)ipow_ll(np1, t->dim) >= 2147483647.0)
+    return *why = "tree too large: (3^depth+1)^dim must be < 2^31", false;
+  return true;
+}
+
+// Carves every array of the handle (measure-only when base is null).
+void carve(adafac_handle h, Carver& cv) {
+  const int D = h->D, L = h->L;
+  const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
+  const bool boxmg = h->opt.transfer == ADAFAC_TRANSFER_BOXMG;
+  const bool exact = h->opt.rtilde == ADAFAC_RTILDE_EXACT && h->opt.variant == ADAFAC_VARIANT_JAC;
+  const bool fas = h->opt.form == ADAFAC_FORM_FAS;
+  const int NC = 1 << D, NS = D == 2 ? 9 : 27;
+  for (int l = 1; l <= L; ++l) {
+    LevelData& lv = h->lev[l];
+    lv.n = (int)ipow_ll(3, l);
+    lv.V = ipow_ll(lv.n + 1, D);
+    const long long ncell = ipow_ll(lv.n, D);
+    // decisions depend on the configuration only, never on pointers: the
+    // measuring pass (base == nullptr) must carve exactly what the real one does
+    const bool stored = l < L && !h->uniform;
+    const bool has_p = l >= 2 && boxmg;
+    lv.invd = cv.take<double>(lv.V);
+    if (stored) {
+      lv.st = cv.take<double>(NS * lv.V);
+      lv.Kc = cv.take<double>((long long)NC * NC * ncell);
+    }
+    if (has_p) lv.P = cv.take<double>(NC * lv.V);
+    lv.r = cv.take<double>(lv.V);  // fine level: FP64 residual / f staging
+    if (!mixed) {
+      if (l < L) {
+        lv.bt = cv.take<double>(lv.V);
+        lv.g = cv.take<double>(lv.V);
+        lv.t = cv.take<double>(lv.V);
+      }
+      if ((exact || fas) && l >= 2) lv.y = cv.take<double>(lv.V);
+      if (fas && l < L) {
+        lv.ul = cv.take<double>(lv.V);
+        lv.bl = cv.take<double>(lv.V);
+      }
+      if (fas && l >= 2) lv.uhat = cv.take<double>(lv.V);
+    } else {
+      lv.invd32 = cv.take<float>(lv.V);
+      if (stored) lv.st32 = cv.take<float>(NS * lv.V);
+      if (has_p) lv.P32 = cv.take<float>(NC * lv.V);
+      lv.r32 = cv.take<float>(lv.V);
+      if (l < L) {
+        lv.bt32 = cv.take<float>(lv.V);
+        lv.g32 = cv.take<float>(lv.V);
+        lv.t32 = cv.take<float>(lv.V);
+      }
+      if (exact && l >= 2) lv.y32 = cv.take<float>(lv.V);
+    }
+  }
+  const long long Vf = h->lev[L].V;
+  h->u = cv.take<double>(Vf);
+  h->b = cv.take<double>(Vf);
+  if (!h->eps_scalar) {
+    h->eps = cv.take<double>(ipow_ll(h->lev[L].n, D));
+    if (mixed) h->eps32 = cv.take<float>(ipow_ll(h->lev[L].n, D));
+  }
+  if (mixed) {
+    h->e32 = cv.take<float>(Vf);
+    h->rhs32 = cv.take<float>(Vf);
+  }
+  h->partials = cv.take<double>(kNormBlocks);
+  h->ctl = cv.take<Control>(1);
+  h->hist = cv.take<double>(kHistCap);
+}
+
+// Reference stencil (eps = 1, without the h^(D-2) factor): the neighbour at
+// offset o shares 2^(D-k) cells with the centre (k non-zero components of o),
+// each contributing K_ref(k).
+void ref_stencil(int D, double* st) {
+  const double k2[3] = {2.0 / 3.0, -1.0 / 6.0, -1.0 / 3.0};
+  const double k3[4] = {1.0 / 3.0, 0.0, -1.0 / 12.0, -1.0 / 12.0};
+  const int NS = D == 2 ? 9 : 27;
+  for (int s = 0; s < NS; ++s) {
+    int t = s, k = 0;
+    for (int j = 0; j < D; ++j) {
+      k += (t % 3) != 1;
+      t /= 3;
+    }
+    st[s] = (double)(1 << (D - k)) * (D == 2 ? k2[k] : k3[k]);
+  }
+}
+
+// The truncated smoothed restriction stencil: (M^-1 A_{eps=1} P e_J) at the
+// fine vertices 3J + o, o in [-2, 2]^D, for d-linear P (Sec. 3.2, option 1),
+// ordered with x fastest.  The mesh width cancels between A and M.
+void smoothed_stencil(int D, double* out) {
+  double st[27];
+  ref_stencil(D, st);
+  const int NS = D == 2 ? 9 : 27;
+  const int N5 = D == 2 ? 25 : 125;
+  const double centre = st[(NS - 1) / 2];
+  for (int k = 0; k < N5; ++k) {
+    int o[3] = {0, 0, 0}, t = k;
+    for (int j = 0; j < D; ++j) {
+      o[j] = t % 5 - 2;
+      t /= 5;
+    }
+    double acc = 0.0;
+    for (int s = 0; s < NS; ++s) {
+      int u = s;
+      double hat = 1.0;
+      for (int j = 0; j < D; ++j) {
+        const int p = o[j] + (u % 3) - 1;
+        u /= 3;
+        const double w = 1.0 - std::fabs((double)p) / 3.0;
+        hat *= w > 0.0 ? w : 0.0;
+      }
+      acc += st[s] * hat;
+    }
+    out[k] = acc / centre;
+  }
+}
+
+template <typename T>
+void fill_uniform_view(LevelView<T>& v, int D, double eps, int n) {
+  double st[27];
+  ref_stencil(D, st);
+  const double hf = D == 2 ? 1.0 : 1.0 / n;
+  v.opkind = OP_UNIFORM;
+  for (int s = 0; s < (D == 2 ? 9 : 27); ++s) v.cst[s] = (T)(eps * hf * st[s]);
+  v.invd0 = (T)(1.0 / (eps * hf * st[D == 2 ? 4 : 13]));
+  v.eps0 = (T)eps;
+}
+
+template <int D>
+adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_in, int on_dev) {
+  const int L = h->L;
+  cudaStream_t s = h->stream;
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  LevelData& fine = h->lev[L];
+  const long long ncf = ipow_ll(fine.n, D);
+  // eps
+  if (!h->eps_scalar) {
+    if (cudaMemcpyAsync(h->eps, eps_in, sizeof(double) * ncf, kind, s) != cudaSuccess)
+      return check_cuda(h, "copy eps");
+  }
+  // right-hand side: f staged in the fine residual array, then b = h^D f
+  if (f_in) {
+    if (cudaMemcpyAsync(fine.r, f_in, sizeof(double) * fine.V, kind, s) != cudaSuccess)
+      return check_cuda(h, "copy f");
+    launch_rhs<D>(fine.r, h->b, fine.n, s);
+  } else {
+    cudaMemsetAsync(h->b, 0, sizeof(double) * fine.V, s);
+  }
+  // level views (FP64)
+  for (int l = 1; l <= L; ++l) {
+    LevelData& lv = h->lev[l];
+    LevelView<double>& v = lv.v64;
+    v = LevelView<double>();
+    v.n = lv.n;
+    v.np1 = lv.n + 1;
+    v.V = lv.V;
+    v.hfac = D == 2 ? 1.0 : 1.0 / lv.n;
+    v.invd = lv.invd;
+    v.boxmg = lv.P ? 1 : 0;
+    v.P = lv.P;
+    if (l == L) {
+      if (h->eps_scalar) {
+        fill_uniform_view(v, D, h->eps0, lv.n);
+        v.invd = lv.invd;
+      } else {
+        v.opkind = OP_EPS;
+        v.eps = h->eps;
+      }
+    } else if (h->uniform) {
+      fill_uniform_view(v, D, h->eps0, lv.n);
+      v.invd = lv.invd;
+    } else {
+      v.opkind = OP_STORED;
+      v.st = lv.st;
+    }
+  }
+  // fine inverse diagonal
+  launch_fine_invdiag<D>(fine.v64, fine.invd, s);
+  // hierarchy: P_l, Galerkin A_{l-1}, assembled stencils
+  for (int l = L; l >= 2; --l) {
+    LevelData& lf = h->lev[l];
+    LevelData& lc = h->lev[l - 1];
+    if (lf.P) {
+      LevelView<double> vf = lf.v64;
+      vf.boxmg = 0;
+      launch_boxmg<D>(vf, lf.P, lc.n, s);
+      if (check_cuda(h, "boxmg") != ADAFAC_OK) return ADAFAC_ERR_CUDA;
+    }
+    if (!h->uniform) {
+      launch_galerkin<D>(lf.v64, l == L ? nullptr : lf.Kc, lc.Kc, lc.n, s);
+      launch_assemble<D>(lc.Kc, lc.st, lc.invd, lc.n, s);
+    } else {
+      launch_fine_invdiag<D>(lc.v64, lc.invd, s);
+    }
+    if (check_cuda(h, "galerkin") != ADAFAC_OK) return ADAFAC_ERR_CUDA;
+  }
+  // cycle parameters
+  double sd[125];
+  smoothed_stencil(D, sd);
+  h->cp64 = CycleParams<double>();
+  h->cp64.variant = h->opt.variant;
+  h->cp64.rtilde_exact = h->opt.rtilde == ADAFAC_RTILDE_EXACT;
+  h->cp64.omega = h->opt.omega;
+  h->cp64.omega_tilde = h->opt.omega_tilde;
+  for (int k = 0; k < 125; ++k) h->cp64.stilde[k] = sd[k];
+  h->cp32 = CycleParams<float>();
+  h->cp32.variant = h->cp64.variant;
+  h->cp32.rtilde_exact = h->cp64.rtilde_exact;
+  h->cp32.omega = (float)h->opt.omega;
+  h->cp32.omega_tilde = (float)h->opt.omega_tilde;
+  for (int k = 0; k < 125; ++k) h->cp32.stilde[k] = (float)sd[k];
+  // FP32 copies for the mixed mode
+  if (h->opt.precision == ADAFAC_PRECISION_MIXED) {
+    const int NC = 1 << D, NS = D == 2 ? 9 : 27;
+    if (h->eps32) launch_to_float(h->eps, h->eps32, ncf, s);
+    for (int l = 1; l <= L; ++l) {
+      LevelData& lv = h->lev[l];
+      launch_to_float(lv.invd, lv.invd32, lv.V, s);
+      if (lv.st) launch_to_float(lv.st, lv.st32, NS * lv.V, s);
+      if (lv.P) launch_to_float(lv.P, lv.P32, NC * lv.V, s);
+      const LevelView<double>& a = lv.v64;
+      LevelView<float>& v = lv.v32;
+      v = LevelView<float>();
+      v.n = a.n;
+      v.np1 = a.np1;
+      v.V = a.V;
+      v.opkind = a.opkind;
+      v.st = lv.st32;
+      v.eps = h->eps32;
+      v.hfac = (float)a.hfac;
+      v.eps0 = (float)a.eps0;
+      for (int k = 0; k < 27; ++k) v.cst[k] = (float)a.cst[k];
+      v.invd = lv.invd32;
+      v.invd0 = (float)a.invd0;
+      v.boxmg = a.boxmg;
+      v.P = lv.P32;
+    }
+    cudaMemsetAsync(h->e32, 0, sizeof(float) * fine.V, s);
+  }
+  cudaMemsetAsync(h->u, 0, sizeof(double) * fine.V, s);
+  Control c{};
+  c.tol = -1.0;
+  c.set_r0 = 1;
+  cudaMemcpyAsync(h->ctl, &c, sizeof(Control), cudaMemcpyHostToDevice, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda(h, "setup");
+  return check_cuda(h, "setup");
+}
+
+double hD_of(adafac_handle h) {
+  return std::pow(1.0 / h->lev[h->L].n, h->D);
+}
+
+// One FP64 cycle (Algorithm 1 or a variant) on u.
+template <int D>
+void fp64_cycle(adafac_handle h) {
+  const int L = h->L;
+  cudaStream_t s = h->stream;
+  LevelData* lv = h->lev;
+  const CycleParams<double>& cp = h->cp64;
+  const bool exact = cp.rtilde_exact && cp.variant == V_JAC;
+  launch_residual<D, double, double>(lv[L].v64, h->u, h->b, lv[L].r, nullptr, h->partials,
+                                     kNormBlocks, hD_of(h), h->ctl, s);
+  launch_norm_finalize(h->partials, kNormBlocks, h->ctl, h->hist, kHistCap, 0, s);
+  h->launches += 2;
+  const bool fas = h->opt.form == ADAFAC_FORM_FAS;
+  if (fas) {
+    // Eq. 4: u_l = I u_{l+1}, u^_{l+1} = u_{l+1} - P u_l,
+    // b_l = R (b_{l+1} - A_{l+1} u^_{l+1}), r_l = b_l - A_l u_l
+    for (int l = L - 1; l >= 1; --l) {
+      const double* uf = l + 1 == L ? h->u : lv[l + 1].ul;
+      const double* bf = l + 1 == L ? h->b : lv[l + 1].bl;
+      launch_inject<D>(uf, lv[l + 1].n, lv[l].ul, h->ctl, s);
+      launch_hierarchical<D>(lv[l + 1].v64, lv[l].v64, uf, lv[l].ul, lv[l + 1].uhat, h->ctl, s);
+      launch_residual<D, double, double>(lv[l + 1].v64, lv[l + 1].uhat, bf, lv[l + 1].y, nullptr,
+                                         nullptr, 0, 0.0, h->ctl, s);
+      launch_restrict_plain<D>(lv[l + 1].v64, lv[l].v64, lv[l + 1].y, lv[l].bl, h->ctl, s);
+      launch_residual<D, double, double>(lv[l].v64, lv[l].ul, lv[l].bl, lv[l].r, nullptr, nullptr,
+                                         0, 0.0, h->ctl, s);
+      h->launches += 5;
+    }
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    const double gscale =
+        cp.variant == V_EXP ? std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0;
+    if (exact) {
+      launch_apply_scaled<D, double>(lv[l + 1].v64, lv[l + 1].r, lv[l + 1].y, h->ctl, s);
+      h->launches += 1;
+    }
+    launch_restrict<D, double>(lv[l + 1].v64, lv[l].v64, cp, lv[l + 1].r, lv[l + 1].y, lv[l].r,
+                               fas ? 1 : 0, lv[l].bt, lv[l].g, gscale, h->ctl, s);
+    h->launches += 1;
+  }
+  // t_1 = g_1; t_l = g_l + P q_{l-1}
+  for (int l = 2; l <= L - 1; ++l) {
+    const double* tc = l - 1 == 1 ? lv[1].g : lv[l - 1].t;
+    launch_prolong<D, double>(lv[l].v64, lv[l - 1].v64, cp, tc, lv[l].g, lv[l].t, h->ctl, s);
+    h->launches += 1;
+  }
+  LevelView<double> empty;
+  const double* tc = L >= 2 ? (L - 1 == 1 ? lv[1].g : lv[L - 1].t) : nullptr;
+  launch_update<D, double, double>(lv[L].v64, L >= 2 ? lv[L - 1].v64 : empty, cp, lv[L].r, tc,
+                                   h->u, h->ctl, s);
+  h->launches += 1;
+}
+
+// One FP32 cycle on the correction equation A e = rhs32 (mixed mode).
+template <int D>
+void fp32_cycle(adafac_handle h) {
+  const int L = h->L;
+  cudaStream_t s = h->stream;
+  LevelData* lv = h->lev;
+  const CycleParams<float>& cp = h->cp32;
+  const bool exact = cp.rtilde_exact && cp.variant == V_JAC;
+  launch_residual<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, nullptr, 0,
+                                   0.0, h->ctl, s);
+  h->launches += 1;
+  for (int l = L - 1; l >= 1; --l) {
+    const float gscale =
+        cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
+    if (exact) {
+      launch_apply_scaled<D, float>(lv[l + 1].v32, lv[l + 1].r32, lv[l + 1].y32, h->ctl, s);
+      h->launches += 1;
+    }
+    launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
+                              lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
+    h->launches += 1;
+  }
+  for (int l = 2; l <= L - 1; ++l) {
+    const float* tc = l - 1 == 1 ? lv[1].g32 : lv[l - 1].t32;
+    launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
+    h->launches += 1;
+  }
+  LevelView<float> empty;
+  const float* tc = L >= 2 ? (L - 1 == 1 ? lv[1].g32 : lv[L - 1].t32) : nullptr;
+  launch_update<D, float, float>(lv[L].v32, L >= 2 ? lv[L - 1].v32 : empty, cp, lv[L].r32, tc,
+                                 h->e32, h->ctl, s);
+  h->launches += 1;
+}
+
+// FP64 residual of u (norm recorded as a cycle evaluation) and its FP32 copy
+// as the right-hand side of the correction equation.
+template <int D>
+void refine_residual(adafac_handle h) {
+  const int L = h->L;
+  launch_residual<D, double, double>(h->lev[L].v64, h->u, h->b, nullptr, h->rhs32, h->partials,
+                                     kNormBlocks, hD_of(h), h->ctl, h->stream);
+  launch_norm_finalize(h->partials, kNormBlocks, h->ctl, h->hist, kHistCap, 0, h->stream);
+  h->launches += 2;
+}
+
+template <int D>
+void mixed_step(adafac_handle h, int k) {
+  refine_residual<D>(h);
+  for (int i = 0; i < k; ++i) fp32_cycle<D>(h);
+  launch_refine_update(h->u, h->e32, h->lev[h->L].V, h->ctl, h->stream);
+  h->launches += 1;
+}
+
+template <int D>
+void enqueue_cycles(adafac_handle h, int n) {
+  if (h->opt.precision == ADAFAC_PRECISION_FP64) {
+    for (int i = 0; i < n; ++i) fp64_cycle<D>(h);
+    return;
+  }
+  while (n > 0) {
+    const int k = n < h->opt.inner_cycles ? n : h->opt.inner_cycles;
+    mixed_step<D>(h, k);
+    n -= k;
+  }
+}
+
+template <int D>
+void enqueue_query(adafac_handle h) {
+  const int L = h->L;
+  launch_residual<D, double, double>(h->lev[L].v64, h->u, h->b, nullptr, nullptr, h->partials,
+                                     kNormBlocks, hD_of(h), nullptr, h->stream);
+  launch_norm_finalize(h->partials, kNormBlocks, h->ctl, h->hist, kHistCap, 1, h->stream);
+  h->launches += 2;
+}
+
+adafac_status read_ctl(adafac_handle h, Control* c) {
+  if (cudaMemcpyAsync(c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream) !=
+      cudaSuccess)
+    return check_cuda(h, "read control");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  return check_cuda(h, "control");
+}
+
+template <typename F>
+adafac_status write_ctl_field(adafac_handle h, size_t offset, const F& value) {
+  if (cudaMemcpyAsync(reinterpret_cast<char*>(h->ctl) + offset, &value, sizeof(F),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return check_cuda(h, "write control");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  return ADAFAC_OK;
+}
+
+__global__ void k_mask_boundary2(double* u, int n) {
+  const int np1 = n + 1;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < (long long)np1 * np1;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(v % np1), y = (int)(v / np1);
+    if (x == 0 || y == 0 || x == n || y == n) u[v] = 0.0;
+  }
+}
+__global__ void k_mask_boundary3(double* u, int n) {
+  const long long np1 = n + 1;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < np1 * np1 * np1;
+       v += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(v % np1), y = (int)((v / np1) % np1), z = (int)(v / (np1 * np1));
+    if (x == 0 || y == 0 || z == 0 || x == n || y == n || z == n) u[v] = 0.0;
+  }
+}
+
+adafac_status reset_control(adafac_handle h) {
+  Control c{};
+  c.tol = -1.0;
+  c.set_r0 = 1;
+  if (cudaMemcpyAsync(h->ctl, &c, sizeof(Control), cudaMemcpyHostToDevice, h->stream) !=
+      cudaSuccess)
+    return check_cuda(h, "reset control");
+  if (h->e32) cudaMemsetAsync(h->e32, 0, sizeof(float) * h->lev[h->L].V, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  return check_cuda(h, "reset");
+}
+
+}  // namespace
+
+extern "C" {
+
+adafac_status adafac_default_options(adafac_options* o) {
+  if (!o) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null options");
+  o->variant = ADAFAC_VARIANT_JAC;
+  o->transfer = ADAFAC_TRANSFER_DLINEAR;
+  o->precision = ADAFAC_PRECISION_FP64;
+  o->rtilde = ADAFAC_RTILDE_TRUNCATED;
+  o->form = ADAFAC_FORM_CS;
+  o->inner_cycles = 12;
+  o->omega = 0.6;
+  o->omega_tilde = 0.6;
+  o->omega_exp = 0.5;
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_workspace_size(const adafac_tree* tree, const adafac_options* opt,
+                                    size_t* bytes) {
+  std::string why;
+  if (!tree || !opt || !bytes) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null argument");
+  if (!valid_tree(tree, &why) || !valid_options(opt, &why))
+    return fail(nullptr, ADAFAC_ERR_INVALID_ARG, why);
+  // The size depends on whether eps is scalar; report the larger (per-cell) case.
+  adafac_handle_s tmp;
+  tmp.D = tree->dim;
+  tmp.L = tree->depth;
+  tmp.opt = *opt;
+  tmp.eps_scalar = 0;
+  tmp.uniform = false;
+  Carver cv;
+  carve(&tmp, cv);
+  // lay the arrays out once more against a fake, never dereferenced base:
+  // both passes must agree, or the size reported here would be wrong
+  Carver check;
+  check.base = reinterpret_cast<char*>(256);
+  carve(&tmp, check);
+  if (check.off != cv.off)
+    return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "internal error: workspace layout mismatch");
+  *bytes = cv.off + 256;
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_setup(const adafac_tree* tree, const double* eps, int eps_is_scalar,
+                           const double* f, int inputs_on_device, const adafac_options* opt,
+                           void* workspace, size_t workspace_bytes, void* stream,
+                           adafac_handle* out) {
+  std::string why;
+  if (!out) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  if (!tree || !opt || !eps) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null argument");
+  if (!valid_tree(tree, &why) || !valid_options(opt, &why))
+    return fail(nullptr, ADAFAC_ERR_INVALID_ARG, why);
+  adafac_handle h = new (std::nothrow) adafac_handle_s();
+  if (!h) return fail(nullptr, ADAFAC_ERR_OOM, "host allocation failed");
+  h->D = tree->dim;
+  h->L = tree->depth;
+  h->opt = *opt;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->eps_scalar = eps_is_scalar ? 1 : 0;
+  if (eps_is_scalar) {
+    if (inputs_on_device) {
+      if (cudaMemcpy(&h->eps0, eps, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        delete h;
+        return fail(nullptr, ADAFAC_ERR_CUDA, "copy scalar eps");
+      }
+    } else {
+      h->eps0 = eps[0];
+    }
+    if (!(h->eps0 > 0.0) || !std::isfinite(h->eps0)) {
+      delete h;
+      return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "eps must be positive and finite");
+    }
+  } else if (!inputs_on_device) {
+    const long long nc = ipow_ll(ipow_ll(3, h->L), h->D);
+    for (long long i = 0; i < nc; ++i)
+      if (!(eps[i] > 0.0) || !std::isfinite(eps[i])) {
+        delete h;
+        return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "eps must be positive and finite");
+      }
+  }
+  h->uniform = h->eps_scalar && opt->transfer == ADAFAC_TRANSFER_DLINEAR;
+  Carver measure;
+  carve(h, measure);
+  const size_t need = measure.off + 256;
+  if (workspace) {
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+      delete h;
+      return fail(nullptr, ADAFAC_ERR_OOM,
+                  "workspace too small or not 256-byte aligned: need " + std::to_string(need));
+    }
+    h->ws = static_cast<char*>(workspace);
+    h->ws_bytes = workspace_bytes;
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return fail(nullptr, ADAFAC_ERR_OOM, "cudaMalloc of " + std::to_string(need) + " bytes failed");
+    }
+    h->ws = static_cast<char*>(p);
+    h->ws_bytes = need;
+    h->own_ws = true;
+  }
+  Carver cv;
+  cv.base = h->ws;
+  carve(h, cv);
+  if (cv.off != measure.off) {
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "internal error: workspace layout mismatch");
+  }
+  // FP64 levels need zeroed vectors (boundary rings stay zero)
+  cudaMemsetAsync(h->ws, 0, need - 256, h->stream);
+  adafac_status st = h->D == 2 ? run_setup<2>(h, eps, f, inputs_on_device)
+                               : run_setup<3>(h, eps, f, inputs_on_device);
+  if (st != ADAFAC_OK) {
+    g_setup_error = h->err;
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return st;
+  }
+  h->launches = 0;
+  *out = h;
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_cycle(adafac_handle h, int n_cycles) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (n_cycles < 0) return fail(h, ADAFAC_ERR_INVALID_ARG, "n_cycles must be >= 0");
+  if (h->D == 2) enqueue_cycles<2>(h, n_cycles);
+  else enqueue_cycles<3>(h, n_cycles);
+  return check_cuda(h, "cycle");
+}
+
+adafac_status adafac_solve(adafac_handle h, double rel_tol, int max_cycles, int* cycles_done,
+                           double* rel) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (!(rel_tol >= 0.0) || max_cycles < 0)
+    return fail(h, ADAFAC_ERR_INVALID_ARG, "rel_tol must be >= 0 and max_cycles >= 0");
+  Control c;
+  adafac_status st = read_ctl(h, &c);
+  if (st != ADAFAC_OK) return st;
+  const int applied0 = c.applied;
+  int zero = 0;
+  if ((st = write_ctl_field(h, offsetof(Control, done), zero)) != ADAFAC_OK) return st;
+  if ((st = write_ctl_field(h, offsetof(Control, tol), rel_tol)) != ADAFAC_OK) return st;
+  const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
+  const int batch = mixed ? h->opt.inner_cycles : 8;
+  int enq = 0;
+  bool done = false, diverged = false;
+  while (enq < max_cycles) {
+    const int k = max_cycles - enq < batch ? max_cycles - enq : batch;
+    if (h->D == 2) enqueue_cycles<2>(h, k);
+    else enqueue_cycles<3>(h, k);
+    enq += k;
+    if ((st = read_ctl(h, &c)) != ADAFAC_OK) return st;
+    done = c.done != 0;
+    diverged = c.diverged != 0;
+    if (done || diverged) break;
+  }
+  if (!done && !diverged) {
+    // residual of the final iterate, recorded like a cycle evaluation
+    if (mixed) {
+      if (h->D == 2) refine_residual<2>(h);
+      else refine_residual<3>(h);
+    } else {
+      // an FP64 cycle starts with the residual; evaluate it without updating
+      if (h->D == 2) enqueue_query<2>(h);
+      else enqueue_query<3>(h);
+    }
+    if ((st = read_ctl(h, &c)) != ADAFAC_OK) return st;
+    if (!mixed) c.rel = c.qrel;
+    done = c.rel <= rel_tol || c.done;
+  }
+  const double reached = c.rel;
+  double minus = -1.0;
+  if ((st = write_ctl_field(h, offsetof(Control, tol), minus)) != ADAFAC_OK) return st;
+  if ((st = write_ctl_field(h, offsetof(Control, done), zero)) != ADAFAC_OK) return st;
+  if (cycles_done) *cycles_done = c.applied - applied0;
+  if (rel) *rel = reached;
+  if (diverged) return fail(h, ADAFAC_ERR_DIVERGED, "residual diverged");
+  if (!done) return fail(h, ADAFAC_ERR_NOT_CONVERGED, "max_cycles reached before rel_tol");
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_residual_norm(adafac_handle h, double* rel, double* abs) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (h->D == 2) enqueue_query<2>(h);
+  else enqueue_query<3>(h);
+  Control c;
+  adafac_status st = read_ctl(h, &c);
+  if (st != ADAFAC_OK) return st;
+  if (rel) *rel = c.qrel;
+  if (abs) *abs = std::sqrt(c.qsq);
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_solution(adafac_handle h, double* dst, int dst_on_device) {
+  if (!h || !dst) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  const size_t bytes = sizeof(double) * h->lev[h->L].V;
+  if (cudaMemcpyAsync(dst, h->u, bytes,
+                      dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess)
+    return check_cuda(h, "copy solution");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  return check_cuda(h, "solution");
+}
+
+adafac_status adafac_set_solution(adafac_handle h, const double* src, int src_on_device) {
+  if (!h || !src) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  const size_t bytes = sizeof(double) * h->lev[h->L].V;
+  if (cudaMemcpyAsync(h->u, src, bytes,
+                      src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return check_cuda(h, "copy iterate");
+  const int n = h->lev[h->L].n;
+  if (h->D == 2) k_mask_boundary2<<<256, 256, 0, h->stream>>>(h->u, n);
+  else k_mask_boundary3<<<1024, 256, 0, h->stream>>>(h->u, n);
+  return reset_control(h);
+}
+
+adafac_status adafac_reset(adafac_handle h) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  cudaMemsetAsync(h->u, 0, sizeof(double) * h->lev[h->L].V, h->stream);
+  return reset_control(h);
+}
+
+adafac_status adafac_get_field(adafac_handle h, int field, int level, double* dst,
+                               int dst_on_device, size_t* count) {
+  if (!h || !count) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  if (level < 1 || level > h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "level out of range");
+  LevelData& lv = h->lev[level];
+  const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
+  const int NC = 1 << h->D, NS = h->D == 2 ? 9 : 27;
+  const double* src64 = nullptr;
+  const float* src32 = nullptr;
+  long long n = lv.V;
+  switch (field) {
+    case ADAFAC_FIELD_U:
+      if (level != h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "U lives on the finest level");
+      src64 = h->u;
+      break;
+    case ADAFAC_FIELD_B:
+      if (level != h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "B lives on the finest level");
+      src64 = h->b;
+      break;
+    case ADAFAC_FIELD_R:
+      if (mixed) src32 = lv.r32;
+      else src64 = lv.r;
+      break;
+    case ADAFAC_FIELD_BT:
+      if (level == h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "BT lives on levels < L");
+      if (mixed) src32 = lv.bt32;
+      else src64 = lv.bt;
+      break;
+    case ADAFAC_FIELD_G:
+      if (level == h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "G lives on levels < L");
+      if (mixed) src32 = lv.g32;
+      else src64 = lv.g;
+      break;
+    case ADAFAC_FIELD_T:
+      if (level == h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "T lives on levels < L");
+      if (mixed) src32 = level == 1 ? lv.g32 : lv.t32;
+      else src64 = level == 1 ? lv.g : lv.t;
+      break;
+    case ADAFAC_FIELD_P:
+      if (!lv.P) return fail(h, ADAFAC_ERR_INVALID_ARG, "P is stored for BoxMG levels >= 2 only");
+      src64 = lv.P;
+      n = NC * lv.V;
+      break;
+    case ADAFAC_FIELD_STENCIL:
+      if (!lv.st) return fail(h, ADAFAC_ERR_INVALID_ARG, "stencil is stored for non-uniform levels < L only");
+      src64 = lv.st;
+      n = NS * lv.V;
+      break;
+    case ADAFAC_FIELD_INVDIAG:
+      src64 = lv.invd;
+      break;
+    default:
+      return fail(h, ADAFAC_ERR_INVALID_ARG, "unknown field");
+  }
+  *count = (size_t)n;
+  if (!dst) return ADAFAC_OK;
+  if (!src64 && !src32) return fail(h, ADAFAC_ERR_INVALID_ARG, "field not allocated in this mode");
+  if (src64) {
+    if (cudaMemcpyAsync(dst, src64, sizeof(double) * n,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+      return check_cuda(h, "copy field");
+  } else {
+    std::vector<float> tmp((size_t)n);
+    if (cudaMemcpyAsync(tmp.data(), src32, sizeof(float) * n, cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+      return check_cuda(h, "copy field");
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+    std::vector<double> wide(tmp.begin(), tmp.end());
+    if (cudaMemcpy(dst, wide.data(), sizeof(double) * n,
+                   dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost) != cudaSuccess)
+      return check_cuda(h, "copy field");
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  return check_cuda(h, "get_field");
+}
+
+adafac_status adafac_history(adafac_handle h, double* dst, int max_entries, int* count) {
+  if (!h || !count) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  Control c;
+  adafac_status st = read_ctl(h, &c);
+  if (st != ADAFAC_OK) return st;
+  const int avail = c.nhist < kHistCap ? c.nhist : kHistCap;
+  *count = avail;
+  if (dst && max_entries > 0) {
+    const int m = avail < max_entries ? avail : max_entries;
+    if (cudaMemcpy(dst, h->hist, sizeof(double) * m, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return check_cuda(h, "copy history");
+  }
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_launch_count(adafac_handle h, uint64_t* count) {
+  if (!h || !count) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  *count = h->launches;
+  return ADAFAC_OK;
+}
+
+const char* adafac_last_error(adafac_handle h) {
+  return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+adafac_status adafac_destroy(adafac_handle h) {
+  if (!h) return ADAFAC_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->own_ws) cudaFree(h->ws);
+  delete h;
+  return ADAFAC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal header of the adAFAC CUDA library: level views passed to kernels
+// by value, and the host-side launch wrappers the engine calls.
+//
+// Geometry: a level with n cells per dimension has np1 = n+1 vertices per
+// dimension, V = np1^D vertices in total, linear index x + np1 (y + np1 z).
+// Cells (n^D) use the same order.  Corner c of a cell has offset bit
+// (c >> j) & 1 along dimension j (x = 0); stencil entry s has offset
+// o_j = (s / 3^j) % 3 - 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adafac {
+
+constexpr int kMaxLevels = 16;
+
+enum OpKind { OP_EPS = 0, OP_STORED = 1, OP_UNIFORM = 2 };
+enum Variant { V_ADDITIVE = 0, V_JAC = 1, V_PI = 2, V_EXP = 3 };
+
+// The operator, inverse diagonal and incoming prolongation of one level, in
+// element type T (double for FP64 work, float for the FP32 cycles).
+template <typename T>
+struct LevelView {
+  int n = 0, np1 = 0;
+  long long V = 0;
+  int opkind = OP_UNIFORM;
+  const T* st = nullptr;     // OP_STORED: 3^D entries per vertex, entry-major
+  const T* eps = nullptr;    // OP_EPS: per-cell eps (n^D)
+  T hfac = 0;                // h^(D-2) of the level
+  T eps0 = 0;                // fine level with scalar eps: the value
+  T cst[27] = {};            // OP_UNIFORM: the stencil
+  const T* invd = nullptr;   // 1/diag per vertex, or nullptr -> invd0
+  T invd0 = 0;
+  int boxmg = 0;             // prolongation from level l-1: 0 d-linear, 1 stored
+  const T* P = nullptr;      // BoxMG: 2^D weights per vertex, entry-major
+};
+
+// Cycle parameters shared by the kernels.
+template <typename T>
+struct CycleParams {
+  int variant = V_JAC;
+  int rtilde_exact = 0;
+  T omega = T(0.6), omega_tilde = T(0.6);
+  T stilde[125] = {};        // truncated smoothed-restriction stencil (5^D)
+};
+
+// Device-side control block (one per handle).
+struct Control {
+  double r0sq;        // ||r_0||_h^2
+  double lastsq;      // last evaluated ||r||_h^2 (cycle evaluations)
+  double rel;         // last normalised residual (cycle evaluations)
+  double tol;         // convergence threshold on rel (solve), or -1
+  double qsq;         // ||r||_h^2 of the last explicit query
+  double qrel;        // its normalised value
+  int done;           // 1 once rel <= tol: later kernels of the batch return
+  int diverged;       // 1 once rel is non-finite or > 1e6
+  int nhist;          // entries written to the history
+  int applied;        // cycles applied (one per update kernel that ran)
+  int set_r0;         // 1: the next norm evaluation defines r_0
+  int pad;
+};
+
+// ---- setup launches (FP64) -------------------------------------------------
+template <int D>
+void launch_rhs(const double* f, double* b, int n, cudaStream_t s);
+template <int D>
+void launch_fine_invdiag(const LevelView<double>& fine, double* invd, cudaStream_t s);
+template <int D>
+void launch_boxmg(const LevelView<double>& fine, double* P, int n_c, cudaStream_t s);
+template <int D>
+void launch_galerkin(const LevelView<double>& fine, const double* Kc_fine,
+                     double* Kc_coarse, int n_c, cudaStream_t s);
+template <int D>
+void launch_assemble(const double* Kc, double* st, double* invd, int n, cudaStream_t s);
+void launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
+void launch_fill(double* dst, double value, long long count, cudaStream_t s);
+
+// ---- cycle launches --------------------------------------------------------
+// r = b - A x at the interior vertices of level `lv` (b may be null = 0);
+// optional FP32 copy r32; optional per-block sums of h^D r^2 into partials.
+template <int D, typename T, typename TX>
+void launch_residual(const LevelView<T>& lv, const TX* x, const TX* b, TX* r,
+                     float* r32, double* partials, int nblocks, double hD,
+                     const Control* ctl, cudaStream_t s);
+// Restriction from fine level lf to coarse level lc and the per-level
+// correction: r_c = P^T r_f (unless given), b~_c, g_c.
+template <int D, typename T>
+void launch_restrict(const LevelView<T>& lf, const LevelView<T>& lc,
+                     const CycleParams<T>& cp, const T* r_f, const T* y_f,
+                     T* r_c, int rc_given, T* bt_c, T* g_c, T gscale,
+                     const Control* ctl, cudaStream_t s);
+// y = A (invd .* r) on level lv (exact smoothed restriction).
+template <int D, typename T>
+void launch_apply_scaled(const LevelView<T>& lv, const T* r, T* y,
+                         const Control* ctl, cudaStream_t s);
+// Prolongation chain on a coarse level l >= 2: t_l = g_l + P q_{l-1} with
+// q = t_{l-1} (- I g_l for adAFAC-PI).
+template <int D, typename T>
+void launch_prolong(const LevelView<T>& lf, const LevelView<T>& lc,
+                    const CycleParams<T>& cp, const T* t_c, const T* g_f, T* t_f,
+                    const Control* ctl, cudaStream_t s);
+// Fine update x += c_L + P q_{L-1}, c_L = omega invd r_L.
+template <int D, typename T, typename TX>
+void launch_update(const LevelView<T>& lf, const LevelView<T>& lc,
+                   const CycleParams<T>& cp, const T* r_f, const T* t_c, TX* x,
+                   const Control* ctl, cudaStream_t s);
+// FAS: hierarchical u^_f = u_f - P I u_f (u_f given on level lf; the injected
+// coarse values are read at stride 3).
+template <int D>
+void launch_hierarchical(const LevelView<double>& lf, const LevelView<double>& lc,
+                         const double* u_f, const double* u_c, double* uhat,
+                         const Control* ctl, cudaStream_t s);
+template <int D>
+void launch_inject(const double* u_f, int n_f, double* u_c, const Control* ctl,
+                   cudaStream_t s);
+template <int D>
+void launch_restrict_plain(const LevelView<double>& lf, const LevelView<double>& lc,
+                           const double* r_f, double* b_c, const Control* ctl,
+                           cudaStream_t s);
+// Sums the partials of one norm evaluation (fixed order), records history,
+// sets done / diverged.
+// query != 0: only qsq/qrel (and r_0 when set_r0) are written, regardless of
+// done/diverged.
+void launch_norm_finalize(const double* partials, int nblocks, Control* ctl,
+                          double* hist, int hist_cap, int query, cudaStream_t s);
+// MIXED: u += e, e = 0.
+void launch_refine_update(double* u, float* e, long long V, const Control* ctl,
+                          cudaStream_t s);
+
+}  // namespace adafac

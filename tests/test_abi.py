@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/adafac.h; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1903_10367_gb300 import adafac
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "adafac.h")).read()
+    return sorted(set(re.findall(r"\b(adafac_[a-z_]+)\s*\(", text)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = adafac.load()
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding declares exactly the header's entry points
+    assert sorted(n for n, _, _ in adafac._SIGNATURES) == names
+
+
+def test_library_is_in_tree():
+    lib = adafac.load()
+    assert os.path.commonpath([lib._name, ROOT]) == ROOT
+
+
+def test_default_options():
+    o = adafac.default_options()
+    assert (o.variant, o.transfer, o.precision, o.rtilde, o.form) == (1, 0, 0, 0, 0)
+    assert o.omega == 0.6 and o.omega_tilde == 0.6 and o.inner_cycles >= 1
+
+
+def test_workspace_size_grows_with_depth_and_mixed_needs_fp32_copies():
+    o = adafac.default_options()
+    s3 = adafac.workspace_size(2, 3, o)
+    s4 = adafac.workspace_size(2, 4, o)
+    assert 0 < s3 < s4
+    m = adafac.default_options(precision="mixed")
+    assert adafac.workspace_size(2, 4, m) > 0
+
+
+@pytest.mark.parametrize("dim,depth", [(4, 3), (2, 0), (3, 20)])
+def test_invalid_tree_is_rejected(dim, depth):
+    with pytest.raises(adafac.AdafacError) as ei:
+        adafac.workspace_size(dim, depth, adafac.default_options())
+    assert ei.value.status == 1
+
+
+def test_invalid_options_are_rejected():
+    bad = adafac.default_options(form="fas", precision="mixed")
+    with pytest.raises(adafac.AdafacError) as ei:
+        adafac.workspace_size(2, 3, bad)
+    assert "FAS" in str(ei.value)
+    bad = adafac.default_options()
+    bad.inner_cycles = 0
+    with pytest.raises(adafac.AdafacError):
+        adafac.workspace_size(2, 3, bad)
+
+
+def test_setup_rejects_bad_eps_before_touching_the_device():
+    lib = adafac.load()
+    h = ctypes.c_void_p()
+    eps = (ctypes.c_double * 1)(-1.0)
+    o = adafac.default_options()
+    st = lib.adafac_setup(ctypes.byref(adafac.Tree(2, 2)), ctypes.cast(eps, ctypes.c_void_p), 1,
+                          None, 0, ctypes.byref(o), None, 0, None, ctypes.byref(h))
+    assert st == 1 and not h.value
+    assert b"eps" in lib.adafac_last_error(None)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_workspace_layout_is_consistent_for_every_option_combination(dim):
+    # adafac_workspace_size lays the arrays out twice (measuring and against a
+    # fake base) and fails on any difference
+    for variant in adafac.VARIANT:
+        for transfer in adafac.TRANSFER:
+            for precision in adafac.PRECISION:
+                for rtilde in adafac.RTILDE:
+                    for form in adafac.FORM:
+                        if form == "fas" and precision == "mixed":
+                            continue
+                        o = adafac.default_options(variant=variant, transfer=transfer,
+                                                   precision=precision, rtilde=rtilde, form=form)
+                        assert adafac.workspace_size(dim, 3, o) > 0
