@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 adAFAC solver.
+
+One step = one complete solve of the workload to a normalised residual of
+1e-8 (Eq. 10) from u = 0, with the inputs resident in HBM: reset, then the
+number of adAFAC-Jac cycles the solve needs (found in the warm-up).  The
+metric is vertex updates per second (the paper's cost unit: updates of every
+level's unknowns, sum over l of (3^l - 1)^d per cycle) over the whole job;
+ms_per_step is the time to 1e-8.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica (the method needs no
+exchange between independent solves): weak scaling, max time over ranks.
+``--impl reference`` times the CPU FP64 oracle (rank 0 only) on a bounded
+sample of the same workload.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "vertex-updates/s (adAFAC cycles to 1e-8 normalised residual)"
+UNIT = "vertex-updates/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s, p in zip(sm, power) if p > 200.0] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _algorithmic_bytes(kind, w, precision, eps_scalar):
+    """Bytes the method must move per launch of a fine-level kernel: the state
+    read or written once (interior dofs of the finest level)."""
+    N = (3 ** w.depth - 1) ** w.dim
+    eps_b = 0 if eps_scalar else (4 if precision == "mixed" else 8)
+    p_b = (2 ** w.dim) * (4 if precision == "mixed" else 8) if w.transfer == "boxmg" else 0
+    if precision == "mixed":
+        per = {"fine_residual": 4 + 4 + 4 + eps_b,      # e, rhs in; residual out
+               "fine_update": 4 + 4 + 4 + p_b,          # residual, e in; e out
+               "fine_restrict": 4 + p_b,                # residual in
+               "refine": 8 + 8 + 4 + 8 * (not eps_scalar),  # u, b in; rhs32 out
+               "fine_sweep": 4 + 4 + 4 + eps_b + p_b}   # e, rhs in; e out
+    else:
+        per = {"fine_residual": 8 + 8 + 8 + eps_b,
+               "fine_update": 8 + 8 + 8 + p_b,
+               "fine_restrict": 8 + p_b,
+               "refine": 0,
+               "fine_sweep": 8 + 8 + 8 + eps_b + p_b}
+    return per[kind] * N
+
+
+def run_oracle_sample(w, seconds: float):
+    """Times the FP64 oracle's adAFAC-Jac cycles on a bounded sample of the
+    workload: the same problem on a tree one level shallower (1/3^d of the
+    fine grid), as many cycles as fit in ``seconds``."""
+    from oracle import cycle as oc
+    ws = w.with_depth(max(1, w.depth - 1))
+    eps, sc = ws.eps()
+    H = oc.build_hierarchy(ws.dim, ws.depth, eps, sc, ws.f(), ws.transfer)
+    u = np.zeros_like(H.b)
+    upd = sum(ws.level_dofs())
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        u = oc.cycle(H, u)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 adAFAC-Jac cycles of {ws.name} (dim {ws.dim}, depth {ws.depth}: "
+                      f"the workload one level shallower), numpy on 1 host core, {dt:.1f} s"}
+
+
+def bench_reference(args, w):
+    ws_, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import cycle as oc
+    s = w.with_depth(max(1, w.depth - 1))
+    eps, sc = s.eps()
+    H = oc.build_hierarchy(s.dim, s.depth, eps, sc, s.f(), s.transfer)
+    u = np.zeros_like(H.b)
+    for _ in range(args.warmup):
+        u = oc.cycle(H, u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = oc.cycle(H, u)
+    dt = time.perf_counter() - t0
+    upd = sum(s.level_dofs())
+    value = args.steps * upd / dt
+    sample = (f"one FP64 oracle adAFAC-Jac cycle of {s.name} (the workload one level "
+              f"shallower) per step, numpy on 1 host core")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": _config(w, args, None),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def _config(w, args, cycles):
+    return {"workload": w.name, "dim": w.dim, "depth": w.depth,
+            "fine_dofs": (3 ** w.depth - 1) ** w.dim, "dofs_all_levels": sum(w.level_dofs()),
+            "precision": args.precision, "variant": "adAFAC-Jac", "transfer": w.transfer,
+            "rtilde": "truncated", "tol": args.tol, "cycles_per_step": cycles,
+            "l2": "inputs larger than L2" if sum(w.level_dofs()) * 12 > 130e6
+                  else "L2 flushed between steps",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def bench_ours(args, w):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1903_10367_gb300 import adafac
+    adafac.load()
+    eps, sc = w.eps()
+    f = w.f()
+    eps_arg = float(eps[0]) if sc else eps
+    opts = adafac.default_options(transfer=w.transfer, precision=args.precision)
+    S = adafac.Solver(w.dim, w.depth, eps_arg, f, opts)
+    upd_cycle = sum(w.level_dofs())
+    # warm-up: full solves; the cycle count of one solve defines a step
+    cycles = None
+    for i in range(max(args.warmup, 1)):
+        S.reset()
+        c, rel = S.solve(args.tol, args.max_cycles)
+        if cycles is None:
+            cycles = c
+        assert c == cycles, "cycle count of the solve must be reproducible"
+    flush = None
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
+    small = upd_cycle * 12 < 2 * l2_bytes
+    if small:
+        flush = torch.empty(4 * l2_bytes // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if flush is not None:
+            flush.fill_(1.0)
+        S.reset()
+        S.cycle(cycles)
+
+    # timed region
+    clocks = Clocks(dev) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = S.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = S.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    rel_final = S.residual_norm()[0]
+    if not rel_final <= args.tol * 1.0000001:
+        raise RuntimeError(f"solve did not reach the tolerance: {rel_final}")
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * cycles * upd_cycle / (ms / 1e3)
+    # roofline: per-kernel CUDA-event timing over a second timed region
+    S.timing(True)
+    for _ in range(args.steps):
+        step()
+    kinds = ["fine_sweep", "fine_residual", "fine_update", "fine_restrict", "refine"]
+    kt = {k: S.timing_read(k) for k in kinds}
+    S.timing(False)
+    dom = max(kinds, key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    peaks, src = _peaks()
+    alg = _algorithmic_bytes(dom, w, args.precision, sc)
+    achieved = alg / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
+    traffic = _traffic_from_profile(dom, w)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+                "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
+                "algorithmic_bytes_per_launch": alg,
+                "avg_launch_us": 1e3 * dom_ms / dom_n if dom_n else None,
+                "share_of_step": dom_ms / max(1e-9, sum(v[0] for v in kt.values())),
+                "per_kernel_ms": {k: round(v[0] / args.steps, 4) for k, v in kt.items()}}
+    # FP64 single-instance comparator on the same workload (time to 1e-8)
+    fp64 = None
+    if not args.no_fp64_comparator and rank == 0:
+        S64 = adafac.Solver(w.dim, w.depth, eps_arg, f,
+                            adafac.default_options(transfer=w.transfer, precision="fp64"))
+        c64, _ = S64.solve(args.tol, args.max_cycles)
+        S64.reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S64.cycle(c64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"ms_to_tol": e0.elapsed_time(e1), "cycles": c64,
+                "value": c64 * upd_cycle / (e0.elapsed_time(e1) / 1e3), "unit": UNIT}
+        S64.close()
+    # end to end through the public API from pinned host buffers
+    e2e = _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch)
+    S.close()
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else run_oracle_sample(w, args.cpu_seconds)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 cycles + f64 refinement" if args.precision == "mixed" else "f64",
+           "data": "synthetic", "config": _config(w, args, cycles),
+           "time_to_tol_ms": ms / args.steps, "e2e": e2e, "gpu_launches": launches,
+           "roofline": roofline, "clocks": clk, "cpu_baseline": cpu,
+           "fp64_comparator": fp64}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch):
+    """Setup from host buffers, solve to the tolerance, read the solution back."""
+    if args.e2e_steps <= 0:
+        return None
+    f_pin = torch.from_numpy(f).pin_memory()
+    eps_pin = None if sc else torch.from_numpy(eps).pin_memory()
+    out = torch.empty(f.shape, dtype=torch.float64).pin_memory()
+    nbytes = adafac.workspace_size(w.dim, w.depth, opts)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    times = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = adafac.Solver(w.dim, w.depth, float(eps[0]) if sc else eps_pin.numpy(),
+                          f_pin.numpy(), opts, workspace=ws)
+        c, rel = S.solve(args.tol, args.max_cycles)
+        S.solution(out.numpy())
+        t1 = time.perf_counter()
+        S.close()
+        if i > 0:
+            times.append(t1 - t0)
+    t = statistics.mean(times)
+    h2d = f.nbytes + (8 if sc else eps.nbytes)
+    return {"value": cycles * upd_cycle / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(f.nbytes), "ms_per_step": 1e3 * t,
+            "includes": "setup (H2D copies, BoxMG/Galerkin), solve to tol, D2H of u"}
+
+
+def _traffic_from_profile(kind, w):
+    """DRAM bytes per launch of this kernel from the committed ncu summary, if
+    one exists for the current kernel build (profiles/traffic.json)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+        return table.get(w.name, {}).get(kind)
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="poisson3d_d5", choices=sorted(wl.WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-cycles", type=int, default=5000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-comparator", action="store_true")
+    args = ap.parse_args()
+    w = wl.get(args.workload)
+    if args.impl == "reference":
+        bench_reference(args, w)
+    else:
+        bench_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

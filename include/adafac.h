@@ -154,7 +154,8 @@ adafac_status adafac_solution(adafac_handle h, double* dst, int dst_on_device);
 adafac_status adafac_set_solution(adafac_handle h, const double* src,
                                   int src_on_device);
 
-/* Resets u = 0 and r_0 = b.  Asynchronous. */
+/* Resets u = 0, r_0 := the next residual evaluated, and the history.
+ * Asynchronous (a device kernel resets the control block). */
 adafac_status adafac_reset(adafac_handle h);
 
 /* Inspection of internal per-level arrays (for tests and diagnostics).
@@ -192,6 +193,26 @@ adafac_status adafac_history(adafac_handle h, double* dst, int max_entries,
 /* Number of kernel launches the library has enqueued on this handle since
  * setup (setup kernels excluded). */
 adafac_status adafac_launch_count(adafac_handle h, uint64_t* count);
+
+/* Per-kernel device timing with CUDA events recorded on the handle's stream
+ * around every launch of the kernels below (for roofline measurements; the
+ * events add a few microseconds per launch).  adafac_timing(h, 1) starts
+ * recording and clears the accumulators, adafac_timing(h, 0) stops.
+ * adafac_timing_read synchronises and returns, for one kernel kind, the summed
+ * device time in milliseconds and the number of timed launches since the
+ * last adafac_timing(h, 1). */
+enum {
+  ADAFAC_KERNEL_FINE_RESIDUAL = 0, /* residual of the finest level (cycle)   */
+  ADAFAC_KERNEL_FINE_UPDATE = 1,   /* fine-level update x += c_L + P q      */
+  ADAFAC_KERNEL_FINE_RESTRICT = 2, /* restriction from the finest level     */
+  ADAFAC_KERNEL_REFINE = 3,        /* FP64 refinement residual (MIXED)      */
+  ADAFAC_KERNEL_FINE_SWEEP = 4,    /* fused fine sweep (update + residual +
+                                      restriction in one launch)            */
+  ADAFAC_KERNEL_KINDS = 5
+};
+adafac_status adafac_timing(adafac_handle h, int enable);
+adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
+                                 int* launches);
 
 /* Message of the last failing call on h (or of the last failing setup when
  * h is NULL).  The pointer stays valid until the next call on h. */

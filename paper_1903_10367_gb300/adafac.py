@@ -25,6 +25,8 @@ PRECISION = {"fp64": 0, "mixed": 1}
 RTILDE = {"truncated": 0, "exact": 1}
 FORM = {"cs": 0, "fas": 1}
 FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
+KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,
+          "fine_sweep": 4}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DIVERGED", 4: "TIMEOUT", 5: "CUDA",
           6: "NOT_CONVERGED"}
 
@@ -68,6 +70,8 @@ _SIGNATURES = [
     ("adafac_get_field", _I, [_P, _I, _I, _P, _I, ctypes.POINTER(ctypes.c_size_t)]),
     ("adafac_history", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
     ("adafac_launch_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    ("adafac_timing", _I, [_P, _I]),
+    ("adafac_timing_read", _I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     ("adafac_last_error", ctypes.c_char_p, [_P]),
     ("adafac_destroy", _I, [_P]),
 ]
@@ -237,6 +241,16 @@ class Solver:
         c = ctypes.c_uint64()
         _check(self.lib.adafac_launch_count(self.h, ctypes.byref(c)), self.h)
         return c.value
+
+    def timing(self, enable: bool):
+        _check(self.lib.adafac_timing(self.h, int(enable)), self.h)
+
+    def timing_read(self, kind: str):
+        ms = ctypes.c_double()
+        n = ctypes.c_int()
+        _check(self.lib.adafac_timing_read(self.h, KERNEL[kind], ctypes.byref(ms),
+                                           ctypes.byref(n)), self.h)
+        return ms.value, n.value
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -74,6 +74,11 @@ struct adafac_handle_s {
   CycleParams<float> cp32;
   std::string err;
   uint64_t launches = 0;
+  // per-kernel timing (adafac_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks[ADAFAC_KERNEL_KINDS];
 };
 
 namespace {
@@ -89,6 +94,29 @@ adafac_status check_cuda(adafac_handle h, const char* where) {
   if (e != cudaSuccess)
     return fail(h, ADAFAC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
   return ADAFAC_OK;
+}
+
+cudaEvent_t next_event(adafac_handle h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Runs `launch`, bracketed by timing events when timing is on.
+template <typename F>
+void timed(adafac_handle h, int kind, F&& launch) {
+  if (!h->timing || kind >= ADAFAC_KERNEL_KINDS) {
+    launch();
+    return;
+  }
+  cudaEvent_t a = next_event(h), b = next_event(h);
+  cudaEventRecord(a, h->stream);
+  launch();
+  cudaEventRecord(b, h->stream);
+  h->marks[kind].emplace_back(a, b);
 }
 
 bool valid_options(const adafac_options* o, std::string* why) {
@@ -370,8 +398,10 @@ void fp64_cycle(adafac_handle h) {
   LevelData* lv = h->lev;
   const CycleParams<double>& cp = h->cp64;
   const bool exact = cp.rtilde_exact && cp.variant == V_JAC;
-  launch_residual<D, double, double>(lv[L].v64, h->u, h->b, lv[L].r, nullptr, h->partials,
-                                     kNormBlocks, hD_of(h), h->ctl, s);
+  timed(h, ADAFAC_KERNEL_FINE_RESIDUAL, [&] {
+    launch_residual<D, double, double>(lv[L].v64, h->u, h->b, lv[L].r, nullptr, h->partials,
+                                       kNormBlocks, hD_of(h), h->ctl, s);
+  });
   launch_norm_finalize(h->partials, kNormBlocks, h->ctl, h->hist, kHistCap, 0, s);
   h->launches += 2;
   const bool fas = h->opt.form == ADAFAC_FORM_FAS;
@@ -398,8 +428,10 @@ void fp64_cycle(adafac_handle h) {
       launch_apply_scaled<D, double>(lv[l + 1].v64, lv[l + 1].r, lv[l + 1].y, h->ctl, s);
       h->launches += 1;
     }
-    launch_restrict<D, double>(lv[l + 1].v64, lv[l].v64, cp, lv[l + 1].r, lv[l + 1].y, lv[l].r,
-                               fas ? 1 : 0, lv[l].bt, lv[l].g, gscale, h->ctl, s);
+    timed(h, l + 1 == L ? ADAFAC_KERNEL_FINE_RESTRICT : ADAFAC_KERNEL_KINDS, [&] {
+      launch_restrict<D, double>(lv[l + 1].v64, lv[l].v64, cp, lv[l + 1].r, lv[l + 1].y,
+                                 lv[l].r, fas ? 1 : 0, lv[l].bt, lv[l].g, gscale, h->ctl, s);
+    });
     h->launches += 1;
   }
   // t_1 = g_1; t_l = g_l + P q_{l-1}
@@ -410,8 +442,10 @@ void fp64_cycle(adafac_handle h) {
   }
   LevelView<double> empty;
   const double* tc = L >= 2 ? (L - 1 == 1 ? lv[1].g : lv[L - 1].t) : nullptr;
-  launch_update<D, double, double>(lv[L].v64, L >= 2 ? lv[L - 1].v64 : empty, cp, lv[L].r, tc,
-                                   h->u, h->ctl, s);
+  timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] {
+    launch_update<D, double, double>(lv[L].v64, L >= 2 ? lv[L - 1].v64 : empty, cp, lv[L].r,
+                                     tc, h->u, h->ctl, s);
+  });
   h->launches += 1;
 }
 
@@ -423,8 +457,10 @@ void fp32_cycle(adafac_handle h) {
   LevelData* lv = h->lev;
   const CycleParams<float>& cp = h->cp32;
   const bool exact = cp.rtilde_exact && cp.variant == V_JAC;
-  launch_residual<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, nullptr, 0,
-                                   0.0, h->ctl, s);
+  timed(h, ADAFAC_KERNEL_FINE_RESIDUAL, [&] {
+    launch_residual<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, nullptr,
+                                     0, 0.0, h->ctl, s);
+  });
   h->launches += 1;
   for (int l = L - 1; l >= 1; --l) {
     const float gscale =
@@ -433,8 +469,10 @@ void fp32_cycle(adafac_handle h) {
       launch_apply_scaled<D, float>(lv[l + 1].v32, lv[l + 1].r32, lv[l + 1].y32, h->ctl, s);
       h->launches += 1;
     }
-    launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
-                              lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
+    timed(h, l + 1 == L ? ADAFAC_KERNEL_FINE_RESTRICT : ADAFAC_KERNEL_KINDS, [&] {
+      launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
+                                lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
+    });
     h->launches += 1;
   }
   for (int l = 2; l <= L - 1; ++l) {
@@ -444,8 +482,10 @@ void fp32_cycle(adafac_handle h) {
   }
   LevelView<float> empty;
   const float* tc = L >= 2 ? (L - 1 == 1 ? lv[1].g32 : lv[L - 1].t32) : nullptr;
-  launch_update<D, float, float>(lv[L].v32, L >= 2 ? lv[L - 1].v32 : empty, cp, lv[L].r32, tc,
-                                 h->e32, h->ctl, s);
+  timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] {
+    launch_update<D, float, float>(lv[L].v32, L >= 2 ? lv[L - 1].v32 : empty, cp, lv[L].r32,
+                                   tc, h->e32, h->ctl, s);
+  });
   h->launches += 1;
 }
 
@@ -454,8 +494,10 @@ void fp32_cycle(adafac_handle h) {
 template <int D>
 void refine_residual(adafac_handle h) {
   const int L = h->L;
-  launch_residual<D, double, double>(h->lev[L].v64, h->u, h->b, nullptr, h->rhs32, h->partials,
-                                     kNormBlocks, hD_of(h), h->ctl, h->stream);
+  timed(h, ADAFAC_KERNEL_REFINE, [&] {
+    launch_residual<D, double, double>(h->lev[L].v64, h->u, h->b, nullptr, h->rhs32,
+                                       h->partials, kNormBlocks, hD_of(h), h->ctl, h->stream);
+  });
   launch_norm_finalize(h->partials, kNormBlocks, h->ctl, h->hist, kHistCap, 0, h->stream);
   h->launches += 2;
 }
@@ -525,14 +567,8 @@ __global__ void k_mask_boundary3(double* u, int n) {
 }
 
 adafac_status reset_control(adafac_handle h) {
-  Control c{};
-  c.tol = -1.0;
-  c.set_r0 = 1;
-  if (cudaMemcpyAsync(h->ctl, &c, sizeof(Control), cudaMemcpyHostToDevice, h->stream) !=
-      cudaSuccess)
-    return check_cuda(h, "reset control");
+  launch_reset_control(h->ctl, h->stream);
   if (h->e32) cudaMemsetAsync(h->e32, 0, sizeof(float) * h->lev[h->L].V, h->stream);
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
   return check_cuda(h, "reset");
 }
 
@@ -863,6 +899,34 @@ adafac_status adafac_launch_count(adafac_handle h, uint64_t* count) {
   return ADAFAC_OK;
 }
 
+adafac_status adafac_timing(adafac_handle h, int enable) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (enable) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+    for (auto& m : h->marks) m.clear();
+    h->ev_used = 0;
+  }
+  h->timing = enable != 0;
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms, int* launches) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (kind < 0 || kind >= ADAFAC_KERNEL_KINDS)
+    return fail(h, ADAFAC_ERR_INVALID_ARG, "kernel kind out of range");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  double sum = 0.0;
+  for (auto& pr : h->marks[kind]) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+      return check_cuda(h, "event time");
+    sum += ms;
+  }
+  if (total_ms) *total_ms = sum;
+  if (launches) *launches = (int)h->marks[kind].size();
+  return ADAFAC_OK;
+}
+
 const char* adafac_last_error(adafac_handle h) {
   return h ? h->err.c_str() : g_setup_error.c_str();
 }
@@ -870,6 +934,7 @@ const char* adafac_last_error(adafac_handle h) {
 adafac_status adafac_destroy(adafac_handle h) {
   if (!h) return ADAFAC_OK;
   cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->own_ws) cudaFree(h->ws);
   delete h;
   return ADAFAC_OK;

@@ -351,6 +351,20 @@ __global__ void k_norm_finalize(const double* __restrict__ partials, int nblocks
   else if (ctl->tol >= 0.0 && rel <= ctl->tol) ctl->done = 1;
 }
 
+__global__ void k_reset_control(Control* ctl) {
+  ctl->r0sq = 0.0;
+  ctl->lastsq = 0.0;
+  ctl->rel = 0.0;
+  ctl->tol = -1.0;
+  ctl->qsq = 0.0;
+  ctl->qrel = 0.0;
+  ctl->done = 0;
+  ctl->diverged = 0;
+  ctl->nhist = 0;
+  ctl->applied = 0;
+  ctl->set_r0 = 1;
+}
+
 __global__ void k_refine_update(double* __restrict__ u, float* __restrict__ e, long long V,
                                 const Control* ctl) {
   if (halted(ctl)) return;
@@ -425,6 +439,8 @@ void launch_norm_finalize(const double* partials, int nblocks, Control* ctl, dou
                           int hist_cap, int query, cudaStream_t s) {
   k_norm_finalize<<<1, 256, 0, s>>>(partials, nblocks, ctl, hist, hist_cap, query);
 }
+
+void launch_reset_control(Control* ctl, cudaStream_t s) { k_reset_control<<<1, 1, 0, s>>>(ctl); }
 
 void launch_refine_update(double* u, float* e, long long V, const Control* ctl, cudaStream_t s) {
   k_refine_update<<<grid_for(V, kT, kCap), kT, 0, s>>>(u, e, V, ctl);

@@ -124,6 +124,8 @@ void launch_restrict_plain(const LevelView<double>& lf, const LevelView<double>&
 // done/diverged.
 void launch_norm_finalize(const double* partials, int nblocks, Control* ctl,
                           double* hist, int hist_cap, int query, cudaStream_t s);
+// Resets the control block (r_0 taken at the next evaluation, empty history).
+void launch_reset_control(Control* ctl, cudaStream_t s);
 // MIXED: u += e, e = 0.
 void launch_refine_update(double* u, float* e, long long V, const Control* ctl,
                           cudaStream_t s);
