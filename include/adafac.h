@@ -86,10 +86,17 @@ typedef struct {
   double omega;       /* Jacobi damping, default 0.6 (Sec. 5)                */
   double omega_tilde; /* damping-equation Jacobi damping, default 0.6        */
   double omega_exp;   /* base of exponential damping (VARIANT_EXP)           */
+  int path;           /* ADAFAC_PATH_AUTO: fused kernels where the configuration
+                         allows them (3-D, scalar eps, d-linear, MIXED, CS form,
+                         JAC/ADDITIVE/EXP with truncated R~), else one kernel
+                         per level and step; ADAFAC_PATH_LEVELWISE: always the
+                         latter (same arithmetic, other summation order)      */
 } adafac_options;
 
+enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1 };
+
 /* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,
- * inner_cycles 12, omega = omega_tilde = 0.6, omega_exp = 0.5. */
+ * inner_cycles 12, omega = omega_tilde = 0.6, omega_exp = 0.5, path AUTO. */
 adafac_status adafac_default_options(adafac_options* opt);
 
 /* Device bytes a handle for (tree, opt) needs.  Pass at least this much

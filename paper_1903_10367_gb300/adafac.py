@@ -24,6 +24,7 @@ TRANSFER = {"dlinear": 0, "boxmg": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 RTILDE = {"truncated": 0, "exact": 1}
 FORM = {"cs": 0, "fas": 1}
+PATH = {"auto": 0, "levelwise": 1}
 FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
 KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,
           "fine_sweep": 4}
@@ -46,7 +47,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("rtilde", ctypes.c_int),
                 ("form", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double),
-                ("omega_exp", ctypes.c_double)]
+                ("omega_exp", ctypes.c_double), ("path", ctypes.c_int)]
 
 
 _LIB = None
@@ -108,7 +109,7 @@ def default_options(**kw) -> Options:
     _check(lib.adafac_default_options(ctypes.byref(o)))
     for k, v in kw.items():
         table = {"variant": VARIANT, "transfer": TRANSFER, "precision": PRECISION,
-                 "rtilde": RTILDE, "form": FORM}.get(k)
+                 "rtilde": RTILDE, "form": FORM, "path": PATH}.get(k)
         setattr(o, k, table[v] if table and isinstance(v, str) else v)
     return o
 

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libadafac.so")
-SOURCES = ["setup.cu", "cycle.cu", "api.cu"]
-HEADERS = ["engine.h", "common.cuh"]
+SOURCES = ["setup.cu", "cycle.cu", "sweep3.cu", "api.cu"]
+HEADERS = ["engine.h", "common.cuh", "sweep3.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -6,11 +6,13 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
 #include "../../include/adafac.h"
 #include "engine.h"
+#include "sweep3.cuh"
 
 using namespace adafac;
 
@@ -18,6 +20,13 @@ namespace {
 
 constexpr int kHistCap = 8192;
 constexpr int kNormBlocks = 152 * 8;
+constexpr int kRefineZC = 16;    // fine planes per block of the 3-D refinement residual
+constexpr int kSweepZC = 9;      // coarse planes per block of the fused 3-D sweep
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;
+};
 
 thread_local std::string g_setup_error;
 
@@ -79,6 +88,17 @@ struct adafac_handle_s {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks[ADAFAC_KERNEL_KINDS];
+  // fused 3-D path (uniform operator, d-linear transfers, mixed precision)
+  bool fast3 = false;
+  float* e32b = nullptr;     // second correction buffer (ping-pong)
+  int ebase = 0;             // which of e32 / e32b holds zeros at a step start
+  int npartials = 0;
+  Sweep3Params sw;
+  Refine3Params rf;
+  // CUDA graphs of whole cycle batches / refinement steps
+  bool use_graphs = true;
+  cudaStream_t cap = nullptr;
+  std::map<long, Graph> graphs;
 };
 
 namespace {
@@ -128,6 +148,7 @@ bool valid_options(const adafac_options* o, std::string* why) {
   if (o->form == ADAFAC_FORM_FAS && o->precision != ADAFAC_PRECISION_FP64)
     return *why = "FAS form requires FP64 precision", false;
   if (o->inner_cycles < 1) return *why = "inner_cycles must be >= 1", false;
+  if (o->path < 0 || o->path > 1) return *why = "path out of range", false;
   if (!(o->omega > 0.0) || !(o->omega_tilde >= 0.0) || !(o->omega_exp > 0.0))
     return *why = "damping factors must be positive", false;
   return true;
@@ -140,6 +161,18 @@ bool valid_tree(const adafac_tree* t, std::string* why) {
   if ((double)ipow_ll(np1, t->dim) >= 2147483647.0)
     return *why = "tree too large: (3^depth+1)^dim must be < 2^31", false;
   return true;
+}
+
+// The fused 3-D sweeps cover the uniform (scalar eps, d-linear) mixed
+// precision cycles of adAFAC-Jac with the truncated smoothed restriction and
+// of plain / exponentially damped additive multigrid, in correction form.
+bool fast3_eligible(const adafac_handle_s* h) {
+  const adafac_options& o = h->opt;
+  return o.path == ADAFAC_PATH_AUTO && h->D == 3 && h->L >= 2 && h->uniform &&
+         o.precision == ADAFAC_PRECISION_MIXED &&
+         o.form == ADAFAC_FORM_CS && o.rtilde == ADAFAC_RTILDE_TRUNCATED &&
+         (o.variant == ADAFAC_VARIANT_JAC || o.variant == ADAFAC_VARIANT_ADDITIVE ||
+          o.variant == ADAFAC_VARIANT_EXP);
 }
 
 // Carves every array of the handle (measure-only when base is null).
@@ -202,7 +235,13 @@ void carve(adafac_handle h, Carver& cv) {
     h->e32 = cv.take<float>(Vf);
     h->rhs32 = cv.take<float>(Vf);
   }
-  h->partials = cv.take<double>(kNormBlocks);
+  if (h->fast3) h->e32b = cv.take<float>(Vf);
+  h->npartials = kNormBlocks;
+  if (h->fast3) {
+    const int nb = refine3_blocks(h->lev[L].n, kRefineZC);
+    h->npartials = nb > kNormBlocks ? nb : kNormBlocks;
+  }
+  h->partials = cv.take<double>(h->npartials);
   h->ctl = cv.take<Control>(1);
   h->hist = cv.take<double>(kHistCap);
 }
@@ -377,6 +416,53 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     }
     cudaMemsetAsync(h->e32, 0, sizeof(float) * fine.V, s);
   }
+  if (h->fast3) {
+    // stencil classes of the uniform 27-point operator: centre, face, edge, corner
+    const LevelView<double>& a = fine.v64;
+    Sweep3Params& sw = h->sw;
+    sw = Sweep3Params();
+    sw.n = fine.n;
+    sw.nc = h->lev[L - 1].n;
+    sw.zc = kSweepZC;
+    sw.a_c = (float)a.cst[13];
+    sw.a_f = (float)a.cst[12];
+    sw.a_e = (float)a.cst[9];
+    sw.a_k = (float)a.cst[0];
+    sw.w_invd = (float)(h->opt.omega * a.invd0);
+    sw.rhs = h->rhs32;
+    sw.r_c = h->lev[L - 1].r32;
+    sw.bt_c = h->lev[L - 1].bt32;
+    sw.g_c = h->lev[L - 1].g32;
+    sw.c_invd = (float)h->lev[L - 1].v64.invd0;
+    sw.omega = (float)h->opt.omega;
+    sw.omega_t = (float)h->opt.omega_tilde;
+    sw.gscale = h->opt.variant == ADAFAC_VARIANT_EXP ? (float)h->opt.omega_exp : 1.0f;
+    sw.variant = h->opt.variant;
+    for (int k = 0; k < 125; ++k) {
+      const int ox = k % 5 - 2, oy = (k / 5) % 5 - 2, oz = k / 25 - 2;
+      sw.wres[k] = (float)((1.0 - std::abs(ox) / 3.0) * (1.0 - std::abs(oy) / 3.0) *
+                           (1.0 - std::abs(oz) / 3.0));
+      sw.wdamp[k] = (float)sd[k];
+    }
+    sw.u = h->u;
+    sw.ctl = h->ctl;
+    sw.applied = &h->ctl->applied;
+    Refine3Params& rf = h->rf;
+    rf = Refine3Params();
+    rf.n = fine.n;
+    rf.zc = kRefineZC;
+    rf.a_c = a.cst[13];
+    rf.a_f = a.cst[12];
+    rf.a_e = a.cst[9];
+    rf.a_k = a.cst[0];
+    rf.hD = std::pow(1.0 / fine.n, 3);
+    rf.u = h->u;
+    rf.b = h->b;
+    rf.rhs32 = h->rhs32;
+    rf.partials = h->partials;
+    rf.ctl = h->ctl;
+    h->ebase = 0;
+  }
   cudaMemsetAsync(h->u, 0, sizeof(double) * fine.V, s);
   Control c{};
   c.tol = -1.0;
@@ -510,15 +596,136 @@ void mixed_step(adafac_handle h, int k) {
   h->launches += 1;
 }
 
+// Coarse levels L-1 .. 1 of an FP32 cycle whose level L-1 vectors came from a
+// fused sweep: restrictions below L-1, then the prolongation chain up to L-1.
+template <int D>
+void coarse_chain32(adafac_handle h) {
+  const int L = h->L;
+  cudaStream_t s = h->stream;
+  LevelData* lv = h->lev;
+  const CycleParams<float>& cp = h->cp32;
+  for (int l = L - 2; l >= 1; --l) {
+    const float gscale =
+        cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
+    launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
+                              lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
+    h->launches += 1;
+  }
+  for (int l = 2; l <= L - 1; ++l) {
+    const float* tc = l - 1 == 1 ? lv[1].g32 : lv[l - 1].t32;
+    launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
+    h->launches += 1;
+  }
+}
+
+// One refinement step of the fused 3-D path with k >= 1 FP32 cycles:
+//   r = b - A u (FP64), rhs = (float) r;  UP: restrict rhs (cycle 1's up-pass);
+//   k-1 FULL sweeps (down of cycle j-1 + up of cycle j);  DOWNU: down of
+//   cycle k and u += e.  Returns the zero buffer of the next step.
+int fast3_step(adafac_handle h, int k, int ebase) {
+  const int L = h->L;
+  cudaStream_t s = h->stream;
+  Refine3Params rf = h->rf;
+  timed(h, ADAFAC_KERNEL_REFINE, [&] { launch_refine3(rf, s); });
+  launch_norm_finalize(h->partials, refine3_blocks(h->lev[L].n, kRefineZC), h->ctl, h->hist,
+                       kHistCap, 0, s);
+  h->launches += 2;
+  Sweep3Params p = h->sw;
+  p.q = L - 1 == 1 ? h->lev[1].g32 : h->lev[L - 1].t32;
+  float* E[2] = {h->e32, h->e32b};
+  int cur = ebase;
+  p.e_in = E[cur];
+  p.e_out = E[1 - cur];
+  timed(h, ADAFAC_KERNEL_FINE_RESTRICT, [&] { launch_sweep3(p, SWEEP_UP, s); });
+  h->launches += 1;
+  coarse_chain32<3>(h);
+  for (int j = 2; j <= k; ++j) {
+    p.e_in = E[cur];
+    p.e_out = E[1 - cur];
+    timed(h, ADAFAC_KERNEL_FINE_SWEEP, [&] { launch_sweep3(p, SWEEP_FULL, s); });
+    h->launches += 1;
+    coarse_chain32<3>(h);
+    cur ^= 1;
+  }
+  p.e_in = E[cur];
+  p.e_out = E[1 - cur];
+  timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] { launch_sweep3(p, SWEEP_DOWNU, s); });
+  h->launches += 1;
+  return 1 - cur;
+}
+
+// Runs `enqueue` as a CUDA graph captured once per key (replayed afterwards);
+// direct launches while kernel timing is on or when capture is unavailable.
+template <typename F>
+void run_graph(adafac_handle h, long key, F&& enqueue) {
+  if (h->timing || !h->use_graphs) {
+    enqueue();
+    return;
+  }
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      h->use_graphs = false;
+      enqueue();
+      return;
+    }
+    const uint64_t before = h->launches;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->use_graphs = false;
+      enqueue();
+      return;
+    }
+    cudaStream_t saved = h->stream;
+    h->stream = h->cap;
+    enqueue();
+    h->stream = saved;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    const uint64_t kernels = h->launches - before;
+    h->launches = before;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->use_graphs = false;
+      enqueue();
+      return;
+    }
+    Graph gr;
+    gr.exec = ex;
+    gr.kernels = kernels;
+    it = h->graphs.emplace(key, gr).first;
+  }
+  cudaGraphLaunch(it->second.exec, h->stream);
+  h->launches += it->second.kernels;
+}
+
 template <int D>
 void enqueue_cycles(adafac_handle h, int n) {
   if (h->opt.precision == ADAFAC_PRECISION_FP64) {
-    for (int i = 0; i < n; ++i) fp64_cycle<D>(h);
+    while (n > 0) {
+      const int b = n < 8 ? n : 8;
+      run_graph(h, 1000 + b, [&] {
+        for (int i = 0; i < b; ++i) fp64_cycle<D>(h);
+      });
+      n -= b;
+    }
     return;
   }
   while (n > 0) {
     const int k = n < h->opt.inner_cycles ? n : h->opt.inner_cycles;
-    mixed_step<D>(h, k);
+    if (h->fast3) {
+      const int e0 = h->ebase;
+      int e1 = e0;
+      run_graph(h, 4000 + 2 * k + e0, [&] { e1 = fast3_step(h, k, e0); });
+      h->ebase = e0 ^ (k & 1);
+      (void)e1;
+    } else {
+      run_graph(h, 2000 + k, [&] { mixed_step<D>(h, k); });
+    }
     n -= k;
   }
 }
@@ -569,6 +776,8 @@ __global__ void k_mask_boundary3(double* u, int n) {
 adafac_status reset_control(adafac_handle h) {
   launch_reset_control(h->ctl, h->stream);
   if (h->e32) cudaMemsetAsync(h->e32, 0, sizeof(float) * h->lev[h->L].V, h->stream);
+  if (h->e32b) cudaMemsetAsync(h->e32b, 0, sizeof(float) * h->lev[h->L].V, h->stream);
+  h->ebase = 0;
   return check_cuda(h, "reset");
 }
 
@@ -587,6 +796,7 @@ adafac_status adafac_default_options(adafac_options* o) {
   o->omega = 0.6;
   o->omega_tilde = 0.6;
   o->omega_exp = 0.5;
+  o->path = ADAFAC_PATH_AUTO;
   return ADAFAC_OK;
 }
 
@@ -597,22 +807,28 @@ adafac_status adafac_workspace_size(const adafac_tree* tree, const adafac_option
   if (!valid_tree(tree, &why) || !valid_options(opt, &why))
     return fail(nullptr, ADAFAC_ERR_INVALID_ARG, why);
   // The size depends on whether eps is scalar; report the larger (per-cell) case.
-  adafac_handle_s tmp;
-  tmp.D = tree->dim;
-  tmp.L = tree->depth;
-  tmp.opt = *opt;
-  tmp.eps_scalar = 0;
-  tmp.uniform = false;
-  Carver cv;
-  carve(&tmp, cv);
-  // lay the arrays out once more against a fake, never dereferenced base:
-  // both passes must agree, or the size reported here would be wrong
-  Carver check;
-  check.base = reinterpret_cast<char*>(256);
-  carve(&tmp, check);
-  if (check.off != cv.off)
-    return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "internal error: workspace layout mismatch");
-  *bytes = cv.off + 256;
+  // the size depends on whether eps is scalar: report the larger of both
+  size_t most = 0;
+  for (int scalar = 0; scalar <= 1; ++scalar) {
+    adafac_handle_s tmp;
+    tmp.D = tree->dim;
+    tmp.L = tree->depth;
+    tmp.opt = *opt;
+    tmp.eps_scalar = scalar;
+    tmp.uniform = scalar && opt->transfer == ADAFAC_TRANSFER_DLINEAR;
+    tmp.fast3 = fast3_eligible(&tmp);
+    Carver cv;
+    carve(&tmp, cv);
+    // lay the arrays out once more against a fake, never dereferenced base:
+    // both passes must agree, or the size reported here would be wrong
+    Carver check;
+    check.base = reinterpret_cast<char*>(256);
+    carve(&tmp, check);
+    if (check.off != cv.off)
+      return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "internal error: workspace layout mismatch");
+    most = cv.off > most ? cv.off : most;
+  }
+  *bytes = most + 256;
   return ADAFAC_OK;
 }
 
@@ -655,6 +871,7 @@ adafac_status adafac_setup(const adafac_tree* tree, const double* eps, int eps_i
       }
   }
   h->uniform = h->eps_scalar && opt->transfer == ADAFAC_TRANSFER_DLINEAR;
+  h->fast3 = fast3_eligible(h);
   Carver measure;
   carve(h, measure);
   const size_t need = measure.off + 256;
@@ -935,6 +1152,8 @@ adafac_status adafac_destroy(adafac_handle h) {
   if (!h) return ADAFAC_OK;
   cudaStreamSynchronize(h->stream);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->own_ws) cudaFree(h->ws);
   delete h;
   return ADAFAC_OK;

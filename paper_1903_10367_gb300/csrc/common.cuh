@@ -7,12 +7,18 @@ namespace adafac {
 
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
+// Linear index -> coordinates.  Every array of the library has fewer than
+// 2^31 entries, so 32-bit unsigned division suffices (much cheaper than the
+// 64-bit form).
 template <int D>
 __device__ __forceinline__ void decode(long long v, int np1, int* c) {
+  unsigned w = (unsigned)v;
+  const unsigned m = (unsigned)np1;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    c[j] = (int)(v % np1);
-    v /= np1;
+    const unsigned q = w / m;
+    c[j] = (int)(w - q * m);
+    w = q;
   }
 }
 

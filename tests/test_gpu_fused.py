@@ -1,0 +1,104 @@
+"""The fused 3-D sweeps (uniform operator, d-linear transfers, mixed
+precision) against the level-by-level kernels and the FP64 oracle.
+
+Both GPU paths compute the same FP32 cycles on the correction equation with
+FP64 refinement; they differ only in summation order, so their iterates agree
+to FP32 rounding (checked at 2e-5 relative, well above the ~1e-6 observed
+spread and far below any algorithmic difference, which would show up at
+O(1e-2)).  Mathematically the refined iteration equals the FP64 iteration, so
+the oracle's FP64 iterates bound both to the same tolerance.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import cycle as oc
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1903_10367_gb300 import adafac  # noqa: E402
+
+FP32_RTOL = 2e-5
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _solver(L, path, **opt):
+    o = adafac.default_options(precision="mixed", path=path, **opt)
+    return adafac.Solver(3, L, 1.0, wl.manufactured_rhs(3, L), o)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4])
+@pytest.mark.parametrize("variant", ["jac", "additive", "exp"])
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_fused_equals_levelwise_and_oracle(L, variant, k):
+    n_cycles = 2 * k + 1
+    a = _solver(L, "auto", variant=variant, inner_cycles=k, omega_exp=0.7)
+    b = _solver(L, "levelwise", variant=variant, inner_cycles=k, omega_exp=0.7)
+    a.cycle(n_cycles)
+    b.cycle(n_cycles)
+    ua, ub = a.solution(), b.solution()
+    assert _rel(ua, ub) < FP32_RTOL
+    H = oc.build_hierarchy(3, L, [1.0], True, wl.manufactured_rhs(3, L))
+    u = np.zeros_like(H.b)
+    for _ in range(n_cycles):
+        u = oc.cycle(H, u, variant=variant, omega_exp=0.7)
+    assert _rel(ua, u) < FP32_RTOL
+    if L >= 3:
+        # level L-1 vectors of the last cycle come from the fused restriction
+        for f in ("r", "bt", "g"):
+            fa, fb = a.field(f, L - 1), b.field(f, L - 1)
+            assert _rel(fa, fb) < 1e-4, f
+    a.close()
+    b.close()
+
+
+def test_fused_counts_cycles_and_converges_like_levelwise():
+    res = {}
+    for path in ("auto", "levelwise"):
+        S = _solver(4, path)
+        res[path] = S.solve(1e-8, 1000)
+        S.close()
+    assert res["auto"][0] == res["levelwise"][0]
+    assert res["auto"][1] <= 1e-8
+
+
+def test_fused_reset_and_repeated_solves_are_reproducible():
+    S = _solver(3, "auto", inner_cycles=5)
+    c1, r1 = S.solve(1e-8, 500)
+    u1 = S.solution()
+    S.reset()
+    c2, r2 = S.solve(1e-8, 500)
+    assert (c1, r1) == (c2, r2)
+    assert np.array_equal(u1, S.solution())
+    S.close()
+
+
+def test_full_size_poisson3d_d5_mixed_fused():
+    # the 3-D depth-5 workload (243^3 cells, 14.2M unknowns) through the fused
+    # path; the oracle evaluates the FP64 residual of the GPU solution
+    w = wl.get("poisson3d_d5")
+    S = adafac.Solver(3, 5, 1.0, w.f(), adafac.default_options(precision="mixed"))
+    cycles, rel = S.solve(1e-8, 500)
+    u = S.solution()
+    S.close()
+    assert rel <= 1e-8
+    op = fem.LevelOperator.from_eps(3, 243, [1.0], True)
+    b = fem.load_vector(w.f(), 1.0 / 243, 3)
+    r = fem.zero_boundary(b - op.apply(u))
+    assert np.sqrt(np.sum(r ** 2)) / np.sqrt(np.sum(b ** 2)) <= 1.01e-8
+    # O(h^2) error of the manufactured solution against the depth-4 solve
+    err5 = np.abs(u - wl.manufactured_solution(3, 5)).max()
+    w4 = w.with_depth(4)
+    S4 = adafac.Solver(3, 4, 1.0, w4.f(), adafac.default_options(precision="mixed"))
+    S4.solve(1e-10, 500)
+    err4 = np.abs(S4.solution() - wl.manufactured_solution(3, 4)).max()
+    S4.close()
+    assert 8.0 < err4 / err5 < 10.0
