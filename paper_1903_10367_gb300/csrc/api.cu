@@ -2,6 +2,7 @@
 // lifetime, workspace layout, setup orchestration and the per-cycle launch
 // sequences.  Every numerical step runs in the kernels of setup.cu and
 // cycle.cu on the handle's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -21,7 +22,6 @@ namespace {
 constexpr int kHistCap = 8192;
 constexpr int kNormBlocks = 152 * 8;
 constexpr int kRefineZC = 16;    // fine planes per block of the 3-D refinement residual
-constexpr int kSweepZC = 9;      // coarse planes per block of the fused 3-D sweep
 
 struct Graph {
   cudaGraphExec_t exec = nullptr;
@@ -93,6 +93,8 @@ struct adafac_handle_s {
   float* e32b = nullptr;     // second correction buffer (ping-pong)
   int ebase = 0;             // which of e32 / e32b holds zeros at a step start
   int npartials = 0;
+  int ldx = 0;               // row stride of the padded FP32 fine arrays
+  Sweep3Maps maps;
   Sweep3Params sw;
   Refine3Params rf;
   // CUDA graphs of whole cycle batches / refinement steps
@@ -232,10 +234,15 @@ void carve(adafac_handle h, Carver& cv) {
     if (mixed) h->eps32 = cv.take<float>(ipow_ll(h->lev[L].n, D));
   }
   if (mixed) {
-    h->e32 = cv.take<float>(Vf);
-    h->rhs32 = cv.take<float>(Vf);
+    // the fused path stages planes with the tensor memory accelerator, which
+    // needs row strides that are multiples of 16 bytes: pad rows to 4 floats
+    const long long np1 = h->lev[L].n + 1;
+    h->ldx = h->fast3 ? (int)((np1 + 3) / 4 * 4) : (int)np1;
+    const long long Vp = h->fast3 ? (long long)h->ldx * np1 * np1 : Vf;
+    h->e32 = cv.take<float>(Vp);
+    h->rhs32 = cv.take<float>(Vp);
+    if (h->fast3) h->e32b = cv.take<float>(Vp);
   }
-  if (h->fast3) h->e32b = cv.take<float>(Vf);
   h->npartials = kNormBlocks;
   if (h->fast3) {
     const int nb = refine3_blocks(h->lev[L].n, kRefineZC);
@@ -414,7 +421,7 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
       v.boxmg = a.boxmg;
       v.P = lv.P32;
     }
-    cudaMemsetAsync(h->e32, 0, sizeof(float) * fine.V, s);
+    cudaMemsetAsync(h->e32, 0, sizeof(float) * (size_t)h->ldx * (fine.n + 1) * (fine.n + 1), s);
   }
   if (h->fast3) {
     // stencil classes of the uniform 27-point operator: centre, face, edge, corner
@@ -423,13 +430,21 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw = Sweep3Params();
     sw.n = fine.n;
     sw.nc = h->lev[L - 1].n;
-    sw.zc = kSweepZC;
+    {
+      // coarse planes per block: about one wave of blocks at two per SM
+      int dev = 0, nsm = 152;
+      if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const int ncp1 = h->lev[L - 1].n + 1;
+      const int tiles = ((ncp1 + kSweepBJX - 1) / kSweepBJX) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);
+      const int chunks = std::max(1, (2 * nsm) / tiles);
+      sw.zc = std::max(3, (ncp1 + chunks - 1) / chunks);
+    }
     sw.a_c = (float)a.cst[13];
     sw.a_f = (float)a.cst[12];
     sw.a_e = (float)a.cst[9];
     sw.a_k = (float)a.cst[0];
     sw.w_invd = (float)(h->opt.omega * a.invd0);
-    sw.rhs = h->rhs32;
     sw.r_c = h->lev[L - 1].r32;
     sw.bt_c = h->lev[L - 1].bt32;
     sw.g_c = h->lev[L - 1].g32;
@@ -438,19 +453,35 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw.omega_t = (float)h->opt.omega_tilde;
     sw.gscale = h->opt.variant == ADAFAC_VARIANT_EXP ? (float)h->opt.omega_exp : 1.0f;
     sw.variant = h->opt.variant;
+    // S~ by class (|oz|; in-plane distances); the class form is exact because
+    // S~ is symmetric under reflections and permutations of the axes -- checked
+    const int cls_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    double dcls[18];
+    bool filled[18] = {};
+    bool symmetric = true;
     for (int k = 0; k < 125; ++k) {
-      const int ox = k % 5 - 2, oy = (k / 5) % 5 - 2, oz = k / 25 - 2;
-      sw.wres[k] = (float)((1.0 - std::abs(ox) / 3.0) * (1.0 - std::abs(oy) / 3.0) *
-                           (1.0 - std::abs(oz) / 3.0));
-      sw.wdamp[k] = (float)sd[k];
+      const int ax = std::abs(k % 5 - 2), ay = std::abs((k / 5) % 5 - 2), az = std::abs(k / 25 - 2);
+      const int c = 6 * az + cls_of[ay][ax];
+      if (!filled[c]) {
+        dcls[c] = sd[k];
+        filled[c] = true;
+      } else if (std::fabs(dcls[c] - sd[k]) > 1e-14 * (1.0 + std::fabs(sd[k]))) {
+        symmetric = false;
+      }
     }
+    if (!symmetric) return fail(h, ADAFAC_ERR_INVALID_ARG, "smoothed restriction not symmetric");
+    for (int c = 0; c < 18; ++c) sw.dcls[c] = (float)dcls[c];
+    sw.ldx = h->ldx;
     sw.u = h->u;
     sw.ctl = h->ctl;
     sw.applied = &h->ctl->applied;
+    sw.fault = &h->ctl->fault;
+    sw.fault_info = &h->ctl->fault_info[0];
     Refine3Params& rf = h->rf;
     rf = Refine3Params();
     rf.n = fine.n;
     rf.zc = kRefineZC;
+    rf.ldx = h->ldx;
     rf.a_c = a.cst[13];
     rf.a_f = a.cst[12];
     rf.a_e = a.cst[9];
@@ -462,6 +493,11 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     rf.partials = h->partials;
     rf.ctl = h->ctl;
     h->ebase = 0;
+    if (!sweep3_prepare() ||
+        !sweep3_make_maps(h->e32, h->e32b, h->rhs32, fine.n, h->ldx, &h->maps)) {
+      cudaGetLastError();
+      h->fast3 = false;  // no tensor-map encoder: level-by-level kernels
+    }
   }
   cudaMemsetAsync(h->u, 0, sizeof(double) * fine.V, s);
   Control c{};
@@ -634,22 +670,22 @@ int fast3_step(adafac_handle h, int k, int ebase) {
   p.q = L - 1 == 1 ? h->lev[1].g32 : h->lev[L - 1].t32;
   float* E[2] = {h->e32, h->e32b};
   int cur = ebase;
-  p.e_in = E[cur];
   p.e_out = E[1 - cur];
-  timed(h, ADAFAC_KERNEL_FINE_RESTRICT, [&] { launch_sweep3(p, SWEEP_UP, s); });
+  timed(h, ADAFAC_KERNEL_FINE_RESTRICT,
+        [&] { launch_sweep3(p, h->maps, cur, SWEEP_UP, s); });
   h->launches += 1;
   coarse_chain32<3>(h);
   for (int j = 2; j <= k; ++j) {
-    p.e_in = E[cur];
     p.e_out = E[1 - cur];
-    timed(h, ADAFAC_KERNEL_FINE_SWEEP, [&] { launch_sweep3(p, SWEEP_FULL, s); });
+    timed(h, ADAFAC_KERNEL_FINE_SWEEP,
+          [&] { launch_sweep3(p, h->maps, cur, SWEEP_FULL, s); });
     h->launches += 1;
     coarse_chain32<3>(h);
     cur ^= 1;
   }
-  p.e_in = E[cur];
   p.e_out = E[1 - cur];
-  timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] { launch_sweep3(p, SWEEP_DOWNU, s); });
+  timed(h, ADAFAC_KERNEL_FINE_UPDATE,
+        [&] { launch_sweep3(p, h->maps, cur, SWEEP_DOWNU, s); });
   h->launches += 1;
   return 1 - cur;
 }
@@ -744,6 +780,15 @@ adafac_status read_ctl(adafac_handle h, Control* c) {
       cudaSuccess)
     return check_cuda(h, "read control");
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  if (c->fault) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "a bounded device-side wait gave up (mode %d block %d step %d/%d slot %d "
+             "parity %d plane %d thread %d)",
+             c->fault_info[0], c->fault_info[1], c->fault_info[2], c->fault_info[7],
+             c->fault_info[3], c->fault_info[4], c->fault_info[5], c->fault_info[6]);
+    return fail(h, ADAFAC_ERR_TIMEOUT, buf);
+  }
   return check_cuda(h, "control");
 }
 
@@ -775,8 +820,10 @@ __global__ void k_mask_boundary3(double* u, int n) {
 
 adafac_status reset_control(adafac_handle h) {
   launch_reset_control(h->ctl, h->stream);
-  if (h->e32) cudaMemsetAsync(h->e32, 0, sizeof(float) * h->lev[h->L].V, h->stream);
-  if (h->e32b) cudaMemsetAsync(h->e32b, 0, sizeof(float) * h->lev[h->L].V, h->stream);
+  const long long np1 = h->lev[h->L].n + 1;
+  const size_t ebytes = sizeof(float) * (size_t)(h->ldx ? h->ldx : np1) * np1 * np1;
+  if (h->e32) cudaMemsetAsync(h->e32, 0, ebytes, h->stream);
+  if (h->e32b) cudaMemsetAsync(h->e32b, 0, ebytes, h->stream);
   h->ebase = 0;
   return check_cuda(h, "reset");
 }

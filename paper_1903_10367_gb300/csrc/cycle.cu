@@ -363,6 +363,7 @@ __global__ void k_reset_control(Control* ctl) {
   ctl->nhist = 0;
   ctl->applied = 0;
   ctl->set_r0 = 1;
+  ctl->fault = 0;
 }
 
 __global__ void k_refine_update(double* __restrict__ u, float* __restrict__ e, long long V,

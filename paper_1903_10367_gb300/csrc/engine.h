@@ -58,7 +58,8 @@ struct Control {
   int nhist;          // entries written to the history
   int applied;        // cycles applied (one per update kernel that ran)
   int set_r0;         // 1: the next norm evaluation defines r_0
-  int pad;
+  int fault;          // 1: a bounded device-side wait gave up (reported as TIMEOUT)
+  int fault_info[8];  // where it gave up: mode, block, step index, slot, parity, z
 };
 
 // ---- setup launches (FP64) -------------------------------------------------

@@ -2,6 +2,8 @@
 // transfers) and of the z-marching FP64 refinement residual.
 #pragma once
 
+#include <cuda.h>
+
 #include "engine.h"
 
 namespace adafac {
@@ -9,16 +11,17 @@ namespace adafac {
 enum SweepMode { SWEEP_UP = 0, SWEEP_FULL = 1, SWEEP_DOWNU = 2 };
 
 // coarse columns per block (x, y); the z extent is a launch parameter
-constexpr int kSweepBJX = 16, kSweepBJY = 8;
+constexpr int kSweepBJX = 20, kSweepBJY = 8;
+// staged box of a plane: x from 3 J0x - 4 (a 16-byte boundary), 68 x 30 floats
+constexpr int kBoxW = 3 * kSweepBJX + 8, kBoxH = 3 * kSweepBJY + 6;
 
 struct Sweep3Params {
   int n = 0, nc = 0, zc = 0;       // fine cells, coarse cells, coarse planes per block
+  int ldx = 0;                     // row stride of the FP32 fine arrays (multiple of 4)
   // uniform stencil: A e = a_c e + a_f (6 faces) + a_e (12 edges) + a_k (8 corners)
   float a_c = 0, a_f = 0, a_e = 0, a_k = 0;
   float w_invd = 0;                // omega / diag(A_L)
-  const float* e_in = nullptr;     // previous correction (zero buffer for UP)
   float* e_out = nullptr;          // FULL: new correction; DOWNU: zeroed
-  const float* rhs = nullptr;      // right-hand side of the correction equation
   const float* q = nullptr;        // level L-1 vector to prolong
   float* r_c = nullptr;            // level L-1 restricted residual
   float* bt_c = nullptr;           // level L-1 damping right-hand side
@@ -26,26 +29,41 @@ struct Sweep3Params {
   float c_invd = 0;                // 1 / diag(A_{L-1}) (uniform)
   float omega = 0, omega_t = 0, gscale = 1;
   int variant = V_JAC;
-  float wres[125] = {};            // restriction weights w(ox) w(oy) w(oz)
-  float wdamp[125] = {};           // truncated smoothed restriction (omega applied later)
+  // truncated smoothed restriction S~ by class: for |oz| = 0, 1, 2 the weights of
+  // the in-plane distance classes (0,0) (1,0) (2,0) (1,1) (1,2) (2,2)
+  float dcls[18] = {};
   double* u = nullptr;             // DOWNU: u += e
   const Control* ctl = nullptr;
   int* applied = nullptr;          // &ctl->applied
+  int* fault = nullptr;            // &ctl->fault: set when a bounded wait gives up
+  int* fault_info = nullptr;       // &ctl->fault_info[0]
 };
 
 struct Refine3Params {
-  int n = 0, zc = 0;
+  int n = 0, zc = 0, ldx = 0;
   double a_c = 0, a_f = 0, a_e = 0, a_k = 0;
   double hD = 0;
   const double* u = nullptr;
   const double* b = nullptr;
-  float* rhs32 = nullptr;
+  float* rhs32 = nullptr;          // padded FP32 layout (row stride ldx)
   double* partials = nullptr;
   const Control* ctl = nullptr;
 };
 
-void launch_sweep3(const Sweep3Params& p, int mode, cudaStream_t s);
-void sweep3_grid(int nc, int bjx, int bjy, int zc, dim3* grid);
+// Tensor maps of the FP32 fine arrays for the staged loads.
+struct Sweep3Maps {
+  CUtensorMap e[2];
+  CUtensorMap rhs;
+};
+
+// Encodes the tensor maps (host; false when the driver entry point is missing).
+bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Maps* maps);
+size_t sweep3_smem_bytes();
+// Allows the sweeps' dynamic shared memory (once per process and device).
+bool sweep3_prepare();
+void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
+                   cudaStream_t s);
+void sweep3_grid(int nc, int zc, dim3* grid);
 int refine3_blocks(int n, int zc);
 void launch_refine3(const Refine3Params& p, cudaStream_t s);
 
