@@ -120,13 +120,15 @@ def _algorithmic_bytes(kind, w, precision, eps_scalar):
                "fine_update": 4 + 4 + 4 + p_b,          # residual, e in; e out
                "fine_restrict": 4 + p_b,                # residual in
                "refine": 8 + 8 + 4 + 8 * (not eps_scalar),  # u, b in; rhs32 out
-               "fine_sweep": 4 + 4 + 4 + eps_b + p_b}   # e, rhs in; e out
+               "fine_down": 4 + 4 + 4,                  # e, rhs in; e out
+               "fine_up": 4 + 4,                        # e, rhs in
+               "fine_down_u": 4 + 4 + 8 + 8 + 4}        # e, rhs, u in; u, other e out
     else:
         per = {"fine_residual": 8 + 8 + 8 + eps_b,
                "fine_update": 8 + 8 + 8 + p_b,
                "fine_restrict": 8 + p_b,
                "refine": 0,
-               "fine_sweep": 8 + 8 + 8 + eps_b + p_b}
+               "fine_down": 0, "fine_up": 0, "fine_down_u": 0}
     return per[kind] * N
 
 
@@ -265,7 +267,8 @@ def bench_ours(args, w):
     S.timing(True)
     for _ in range(args.steps):
         step()
-    kinds = ["fine_sweep", "fine_residual", "fine_update", "fine_restrict", "refine"]
+    kinds = ["fine_down", "fine_up", "fine_down_u", "fine_residual", "fine_update",
+             "fine_restrict", "refine"]
     kt = {k: S.timing_read(k) for k in kinds}
     S.timing(False)
     dom = max(kinds, key=lambda k: kt[k][0])

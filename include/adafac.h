@@ -211,11 +211,18 @@ adafac_status adafac_launch_count(adafac_handle h, uint64_t* count);
 enum {
   ADAFAC_KERNEL_FINE_RESIDUAL = 0, /* residual of the finest level (cycle)   */
   ADAFAC_KERNEL_FINE_UPDATE = 1,   /* fine-level update x += c_L + P q      */
-  ADAFAC_KERNEL_FINE_RESTRICT = 2, /* restriction from the finest level     */
+  ADAFAC_KERNEL_FINE_RESTRICT = 2, /* restriction from the finest level (on
+                                      the 3-D uniform path: the first up-pass
+                                      of a refinement step)                 */
   ADAFAC_KERNEL_REFINE = 3,        /* FP64 refinement residual (MIXED)      */
-  ADAFAC_KERNEL_FINE_SWEEP = 4,    /* fused fine sweep (update + residual +
-                                      restriction in one launch)            */
-  ADAFAC_KERNEL_KINDS = 5
+  ADAFAC_KERNEL_FINE_DOWN = 4,     /* 3-D uniform path: down-pass, the fine
+                                      update with its residual recomputed  */
+  ADAFAC_KERNEL_FINE_UP = 5,       /* 3-D uniform path: up-pass, residual +
+                                      restriction + damping right-hand side */
+  ADAFAC_KERNEL_FINE_DOWN_U = 6,   /* 3-D uniform path: last down-pass of a
+                                      refinement step, which also adds the
+                                      correction to the FP64 iterate       */
+  ADAFAC_KERNEL_KINDS = 7
 };
 adafac_status adafac_timing(adafac_handle h, int enable);
 adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,

@@ -27,7 +27,7 @@ FORM = {"cs": 0, "fas": 1}
 PATH = {"auto": 0, "levelwise": 1}
 FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
 KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,
-          "fine_sweep": 4}
+          "fine_down": 4, "fine_up": 5, "fine_down_u": 6}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DIVERGED", 4: "TIMEOUT", 5: "CUDA",
           6: "NOT_CONVERGED"}
 

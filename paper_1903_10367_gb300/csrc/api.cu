@@ -431,13 +431,13 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw.n = fine.n;
     sw.nc = h->lev[L - 1].n;
     {
-      // coarse planes per block: about one wave of blocks at two per SM
+      // coarse planes per block: about one wave of blocks at three per SM
       int dev = 0, nsm = 152;
       if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
       const int ncp1 = h->lev[L - 1].n + 1;
       const int tiles = ((ncp1 + kSweepBJX - 1) / kSweepBJX) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);
-      const int chunks = std::max(1, (2 * nsm) / tiles);
+      const int chunks = std::max(1, (3 * nsm) / tiles);
       sw.zc = std::max(3, (ncp1 + chunks - 1) / chunks);
     }
     sw.a_c = (float)a.cst[13];
@@ -493,7 +493,9 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     rf.partials = h->partials;
     rf.ctl = h->ctl;
     h->ebase = 0;
-    if (!sweep3_prepare() ||
+    // the fused sweep evaluates the trilinear stencil without face terms,
+    // which are exactly zero for the d-linear element in 3-D
+    if (a.cst[12] != 0.0 || !sweep3_prepare() ||
         !sweep3_make_maps(h->e32, h->e32b, h->rhs32, fine.n, h->ldx, &h->maps)) {
       cudaGetLastError();
       h->fast3 = false;  // no tensor-map encoder: level-by-level kernels
@@ -654,10 +656,12 @@ void coarse_chain32(adafac_handle h) {
   }
 }
 
-// One refinement step of the fused 3-D path with k >= 1 FP32 cycles:
+// One refinement step of the 3-D uniform path with k >= 1 FP32 cycles:
 //   r = b - A u (FP64), rhs = (float) r;  UP: restrict rhs (cycle 1's up-pass);
-//   k-1 FULL sweeps (down of cycle j-1 + up of cycle j);  DOWNU: down of
-//   cycle k and u += e.  Returns the zero buffer of the next step.
+//   for cycles j = 2 .. k: DOWN (down-pass of cycle j-1, e into the other
+//   buffer), UPE (up-pass of cycle j from that e), coarse levels;
+//   DOWNU: down-pass of cycle k and u += e.  Returns the zero buffer of the
+//   next step.
 int fast3_step(adafac_handle h, int k, int ebase) {
   const int L = h->L;
   cudaStream_t s = h->stream;
@@ -670,21 +674,20 @@ int fast3_step(adafac_handle h, int k, int ebase) {
   p.q = L - 1 == 1 ? h->lev[1].g32 : h->lev[L - 1].t32;
   float* E[2] = {h->e32, h->e32b};
   int cur = ebase;
-  p.e_out = E[1 - cur];
   timed(h, ADAFAC_KERNEL_FINE_RESTRICT,
         [&] { launch_sweep3(p, h->maps, cur, SWEEP_UP, s); });
   h->launches += 1;
   coarse_chain32<3>(h);
   for (int j = 2; j <= k; ++j) {
     p.e_out = E[1 - cur];
-    timed(h, ADAFAC_KERNEL_FINE_SWEEP,
-          [&] { launch_sweep3(p, h->maps, cur, SWEEP_FULL, s); });
-    h->launches += 1;
+    timed(h, ADAFAC_KERNEL_FINE_DOWN, [&] { launch_sweep3(p, h->maps, cur, SWEEP_DOWN, s); });
+    timed(h, ADAFAC_KERNEL_FINE_UP, [&] { launch_sweep3(p, h->maps, 1 - cur, SWEEP_UPE, s); });
+    h->launches += 2;
     coarse_chain32<3>(h);
     cur ^= 1;
   }
   p.e_out = E[1 - cur];
-  timed(h, ADAFAC_KERNEL_FINE_UPDATE,
+  timed(h, ADAFAC_KERNEL_FINE_DOWN_U,
         [&] { launch_sweep3(p, h->maps, cur, SWEEP_DOWNU, s); });
   h->launches += 1;
   return 1 - cur;

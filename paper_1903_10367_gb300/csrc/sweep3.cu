@@ -1,32 +1,36 @@
-// Fused fine-level sweeps for 3-D trees whose finest operator is uniform
-// (scalar eps) and whose transfers are d-linear: the hot path of the mixed
-// precision cycle.
+// Fine-level sweeps for 3-D trees whose finest operator is uniform (scalar
+// eps) and whose transfers are d-linear: the hot path of the mixed precision
+// cycle.  Each FP32 cycle visits the finest level in two sweeps:
 //
-// One FULL sweep does, in a single pass over the finest level,
-//   down of cycle k-1:  e_{k-1} = e_{k-2} + omega M^-1 (rhs - A e_{k-2}) + P q
-//   up of cycle k:      rho_k = rhs - A e_{k-1},
-//                       r_{L-1} = P^T rho_k,  b~_{L-1} = omega S~^T rho_k,
-//                       g_{L-1} = M^-1 (omega r_{L-1} - omega~ b~_{L-1})
-// (Algorithm 1 / Eq. 9 with c_L = omega M^-1 rho).  The residual of the
-// previous cycle is recomputed on a halo instead of being stored, so the
-// sweep reads e_{k-2} and rhs and writes e_{k-1}: 12 bytes per unknown.
-// UP is the first up-pass of a refinement step (rho = rhs, restriction only);
-// DOWNU is the last down-pass, which adds e to the FP64 iterate u.
+//   DOWN   down-pass of cycle j-1 (the fine-level part of the update of
+//          Algorithm 1 / Eq. 9, with c_L = omega M^-1 rho):
+//            e_{j-1} = e_{j-2} + omega M^-1 (rhs - A e_{j-2}) + P q_{j-1}
+//          where q is the prolonged coarse part of the cycle;
+//   UPE    up-pass of cycle j:  rho = rhs - A e_{j-1},
+//            r_{L-1} = P^T rho,  b~_{L-1} = omega S~^T rho   (Eq. 8),
+//            g_{L-1} = M^-1 (omega r_{L-1} - omega~ b~_{L-1});
+//   UP     the first up-pass of a refinement step (e = 0, so rho = rhs);
+//   DOWNU  the last down-pass, which adds e to the FP64 iterate u and clears
+//          the other correction buffer for the next refinement step.
+// The down-pass recomputes the residual it needs instead of reading a stored
+// one: DOWN reads e and rhs and writes e (12 bytes per unknown), UPE reads e
+// and rhs (8 bytes per unknown).
 //
 // Blocking.  A block owns BJX x BJY coarse columns of level L-1 and zc coarse
 // planes, i.e. the fine vertices whose nearest coarse vertex lies in that box
 // (3 per coarse vertex and direction), and marches through its fine planes in
 // z.  A ring of NSTAGE shared-memory slots is filled by the tensor memory
-// accelerator PREF planes ahead of use: one slot holds a 68 x 30 box of e_{k-2}
-// (owned box + 3, the x origin on a 16-byte boundary) and of rhs; the
-// elected thread arms the slot's mbarrier with the byte count and issues both
-// copies; out-of-domain parts are zero-filled.  Stage B forms e_{k-1} on the
-// owned box + 2, stage C rho_k on the owned box + 1 (the restriction
-// support); the restriction and the damping right-hand side of the block's
-// coarse columns accumulate as planes pass.  Every thread keeps one column
-// and a strip of rows for stages B and C; a 27-point stencil is split into an
-// in-plane part W_p and an off-plane part Y_p per plane,
-// A e(s) = W_s + Y_{s-1} + Y_{s+1}, both kept in registers as planes roll by.
+// accelerator PREF planes ahead of use: a slot holds a 68 x 30 box of e (the
+// owned box + 3 in x and y, its x origin on a 16-byte boundary) and of rhs;
+// one thread arms the slot's mbarrier with the byte count and issues the
+// copies; parts outside the domain are zero-filled.  A thread owns a pair of
+// adjacent columns and a strip of rows and works on the pair with packed
+// FP32x2 arithmetic.  The 27-point stencil is split into an in-plane part W_p
+// and an off-plane part Y_p per plane, A e(s) = W_s + Y_{s-1} + Y_{s+1}; the
+// partial sum W_s + Y_{s-1} and Y_s roll along in registers.  UPE forms rho on
+// the owned box + 1 (the support of the restriction) in shared memory and
+// accumulates the restriction and the damping right-hand side of the block's
+// coarse columns as the planes pass.
 #include "common.cuh"
 #include "sweep3.cuh"
 
@@ -34,40 +38,45 @@ namespace adafac {
 
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 128;                     // threads: 32 column pairs x 4 strips
 constexpr int BJX = kSweepBJX, BJY = kSweepBJY;
-constexpr int OW = 3 * BJX, OH = 3 * BJY;   // owned fine box (x, y)
-constexpr int NCOL = 64;                    // thread columns
-constexpr int NSTRIP = NT / NCOL;           // thread strips
-constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane
+constexpr int OW = 3 * BJX, OH = 3 * BJY;   // owned fine box (x, y): 60 x 24
+constexpr int NPAIR = 32;                   // thread column pairs
+constexpr int NSTRIP = NT / NPAIR;          // thread row strips
+constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane: 68 x 30
 constexpr int PLANE_F = 2048;               // floats per staged plane (128-byte multiple)
-constexpr int NSTAGE = 4, PREF = 2;         // ring slots, planes staged ahead
-constexpr int QH = BJY + 4;                 // coarse rows of the q window (origin J0y - 2)
-constexpr int NQX = QH * NCOL;              // x-interpolated coarse values per plane
+constexpr int NSTAGE = 4, PREF = 3;         // ring slots, planes staged ahead
+constexpr int QW = BJX + 4, QH = BJY + 4;   // coarse q window, origin (J0x - 2, J0y - 2)
+constexpr int NQX = QH * 64;                // x-interpolated coarse values per plane
 constexpr int NJ = BJX * BJY;               // coarse columns of a block
-constexpr int SB_F = 64 * 28, SR_F = 62 * 26 + 4;
+constexpr int RB = OH / NSTRIP;             // down-pass rows per strip
+constexpr int CH = OH + 2, RC = (CH + NSTRIP - 1) / NSTRIP;  // up-pass rows, per strip
+constexpr int SR_P = 64;                    // pitch of the up-pass residual plane
 constexpr long kWaitLimit = 1L << 24;       // polls before a wait gives up
 static_assert(BOXW * BOXH <= PLANE_F, "staged box fits its slot");
-static_assert(NJ <= NT && NQX % NT == 0, "thread counts");
 static_assert((BOXW * 4) % 16 == 0, "box rows are 16-byte multiples");
+static_assert(OW == 2 * (NPAIR - 2) && OH % NSTRIP == 0, "thread tiling of the owned box");
+static_assert(NJ <= 2 * NT && NQX % NT == 0, "thread counts");
+// the slot refilled at step t (that of t + PREF) was last read at step
+// t + PREF - NSTAGE <= t - 1, before the block barrier that opens step t
+static_assert(PREF < NSTAGE, "prefetch distance");
 
-// smem layout (floats): ring slots (e, rhs), sB, sR, sQX[2]; then mbarriers
-constexpr int OFF_SB = NSTAGE * 2 * PLANE_F;
-constexpr int OFF_SR = OFF_SB + SB_F;
-constexpr int OFF_QX = OFF_SR + SR_F;
-constexpr int OFF_BAR = OFF_QX + 2 * NQX;   // 8-byte aligned (even float index)
+// smem layout (floats): ring slots (e, rhs); then either the residual plane
+// sR (up-passes) or the coarse windows sQ[2], sQX[2] (down-passes); mbarriers
+constexpr int OFF_SR = NSTAGE * 2 * PLANE_F;
+constexpr int OFF_Q = OFF_SR;
+constexpr int OFF_QX = OFF_Q + 2 * QW * QH;
+constexpr int END_SR = OFF_SR + SR_P * CH, END_Q = OFF_QX + 2 * NQX;
+constexpr int OFF_BAR = END_SR > END_Q ? END_SR : END_Q;
 constexpr size_t SMEM_BYTES = (size_t)OFF_BAR * 4 + NSTAGE * 8 + 16;
+static_assert(OFF_SR % 2 == 0 && OFF_QX % 2 == 0 && OFF_BAR % 2 == 0, "8-byte alignment");
 
-template <int MODE>
-struct Geo {
-  // stage B (new e) and stage C (new residual) relative to the staged box
-  static constexpr int BX0 = MODE == SWEEP_FULL ? 1 : 3;
-  static constexpr int BW = MODE == SWEEP_FULL ? 64 : 60;
-  static constexpr int BH = MODE == SWEEP_FULL ? 28 : 24;
-  static constexpr int RB = BH / NSTRIP;
-  static constexpr int CW = 62, CH = 26, RC = (CH + NSTRIP - 1) / NSTRIP;
-  static_assert(RB * NSTRIP == BH, "stage B strips tile the region");
-};
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -109,56 +118,86 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* tm, in
       : "memory");
 }
 
+// in-plane sums of a row at a column pair whose first column is odd: the
+// aligned pairs a = (c-1, c), b = (c+1, c+2) give the centre pair (a.y, b.x)
+// and the sum of the x-neighbours h = a + b
+struct RowPair {
+  float2 h, c;
+};
+__device__ __forceinline__ RowPair row_pair(const float* p) {
+  const float2 a = ld2(p), b = ld2(p + 2);
+  RowPair r;
+  r.h = add2(a, b);
+  r.c = make_float2(a.y, b.x);
+  return r;
+}
+
+// in-plane part W and off-plane part Y of the stencil at a row pair, from the
+// rows above (up), at (ce) and below (dn): with X the face neighbours in the
+// plane and D the in-plane diagonal ones,
+//   W = a_c e + a_e D,  Y = a_e (e + X) + a_k D   (a_f = 0 in 3-D)
+struct Parts {
+  float2 W, Y;
+};
+__device__ __forceinline__ Parts parts(const RowPair& up, const RowPair& ce, const RowPair& dn,
+                                       float2 ac2, float2 ae2, float2 ak2) {
+  const float2 X = add2(add2(ce.h, up.c), dn.c);
+  const float2 D = add2(up.h, dn.h);
+  Parts q;
+  q.W = fma2(ac2, ce.c, mul2(ae2, D));
+  q.Y = fma2(ae2, X, mul2(ak2, D));
+  return q;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, 3)
     k_sweep3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
              const __grid_constant__ CUtensorMap tm_rhs) {
-  using G = Geo<MODE>;
-  constexpr bool HAS_B = MODE != SWEEP_UP;
-  constexpr bool FULL = MODE == SWEEP_FULL;
-  constexpr int RB = G::RB, RC = G::RC;
-  extern __shared__ __align__(1024) float smem[];
+  constexpr bool DOWNP = MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU;
+  constexpr bool LOAD_E = MODE != SWEEP_UP;
+  extern __shared__ __align__(128) float smem[];
   __shared__ int s_fail;
   if (halted(p.ctl)) return;
-  if (MODE != SWEEP_UP && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
-      threadIdx.x == 0 && p.applied)
+  if (DOWNP && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      p.applied)
     atomicAdd(p.applied, 1);  // one down-pass (a cycle's update) per launch
 
-  float* sB = smem + OFF_SB;
   float* sR = smem + OFF_SR;
+  float* sQ = smem + OFF_Q;
   float* sQX = smem + OFF_QX;
   const uint32_t bar0 = smem_addr(smem + OFF_BAR);
 
   const int n = p.n, nc = p.nc, ncp1 = nc + 1, ldx = p.ldx;
   const long long fplane = (long long)ldx * (n + 1);
   const int tid = threadIdx.x;
-  const int col = tid % NCOL, strip = tid / NCOL;
+  const int pc = tid % NPAIR, strip = tid / NPAIR;
   const int Jx0 = blockIdx.x * BJX, Jy0 = blockIdx.y * BJY;
   const int Jz0 = blockIdx.z * p.zc;
   const int Jz1 = min(Jz0 + p.zc, ncp1);
   const int xA = 3 * Jx0 - 4, yA = 3 * Jy0 - 4;            // staged box origin
   const int oz0 = 3 * Jz0 - 1, oz1 = 3 * Jz1 - 1;          // owned planes [oz0, oz1)
-  const int zB0 = FULL ? oz0 - 2 : oz0, zB1 = FULL ? oz1 + 2 : oz1;
-  const int zC0 = oz0 - 1, zC1 = oz1 + 1;
+  const int zC0 = oz0 - 1, zC1 = oz1 + 1;                  // up-pass residual planes
+  // step t stages e plane t and rhs plane t-1 (UP: rhs plane t).  Down-passes
+  // update plane s = t-1 (W + Y of plane s-1.. s+1 known at step t), UPE forms
+  // the residual of plane t-1, UP restricts rhs plane t.
   int t0, t1;
-  if (FULL) {
-    t0 = zB0 - 1;
-    t1 = zC1 + 2;
-  } else if (MODE == SWEEP_DOWNU) {
-    t0 = zB0 - 1;
-    t1 = zB1 + 1;
+  if (DOWNP) {
+    t0 = oz0 - 1;
+    t1 = oz1 + 1;
+  } else if (MODE == SWEEP_UPE) {
+    t0 = zC0 - 1;
+    t1 = zC1 + 1;
   } else {
     t0 = zC0;
     t1 = zC1;
   }
-  constexpr uint32_t kBytes = (HAS_B ? 2 : 1) * BOXW * BOXH * 4;
-  // the copies of step t: e plane t and rhs plane t-1 (UP: rhs plane t)
+  constexpr uint32_t kBytes = (LOAD_E ? 2 : 1) * BOXW * BOXH * 4;
   auto issue = [&](int t) {
     const int k = (t - t0) % NSTAGE;
     const uint32_t bar = bar0 + 8 * k;
     float* slot = smem + k * 2 * PLANE_F;
     mbar_expect(bar, kBytes);
-    if (HAS_B) {
+    if (LOAD_E) {
       tma_load(smem_addr(slot), &tm_e, xA, yA, t, bar);
       tma_load(smem_addr(slot + PLANE_F), &tm_rhs, xA, yA, t - 1, bar);
     } else {
@@ -174,88 +213,106 @@ __global__ void __launch_bounds__(NT, 2)
   if (tid == 0)
     for (int t = t0; t < t0 + PREF && t < t1; ++t) issue(t);
 
-  // ---- per-thread geometry, fixed for the whole z march -------------------
-  // stage B: column col, rows strip RB + i of the stage-B region
-  const int xb = xA + G::BX0 + col;
-  const bool inxB = HAS_B && col < G::BW && xb >= 1 && xb <= n - 1;
-  float mB[RB];
-  int qkB[RB];
+  // ---- down-pass geometry: the pair (2 pc, 2 pc + 1) of the owned box is box
+  // columns 3 + 2 pc (+1); row strip RB + i is box row 3 + strip RB + i
+  const int xb = xA + 3 + 2 * pc;                          // odd: 3 J0x - 1 + 2 pc
+  const bool pairB = DOWNP && pc < OW / 2;
+  const float2 mxB = make_float2(pairB && xb >= 1 && xb <= n - 1 ? 1.f : 0.f,
+                                 pairB && xb + 1 >= 1 && xb + 1 <= n - 1 ? 1.f : 0.f);
+  const int y0 = yA + 3 + strip * RB;
+  float myB[RB];
+  int qrB[RB];
   float tyB[RB];
 #pragma unroll
   for (int i = 0; i < RB; ++i) {
-    const int y = yA + G::BX0 + strip * RB + i;
-    mB[i] = (inxB && y >= 1 && y <= n - 1) ? 1.f : 0.f;
+    const int y = y0 + i;
+    myB[i] = y >= 1 && y <= n - 1 ? 1.f : 0.f;
     const int Oy = min(max(y, 0) / 3, nc - 1);
-    qkB[i] = (Oy - (Jy0 - 2)) * NCOL + col;
+    qrB[i] = (Oy - (Jy0 - 2)) * 64 + 2 * pc;
     tyB[i] = (float)(y - 3 * Oy) * (1.f / 3.f);
   }
-  // stage C (FULL): column col, rows strip RC + i of the stage-C region
-  const int xc = xA + 2 + col;
-  const bool inxC = FULL && col < G::CW && xc >= 1 && xc <= n - 1;
-  const int ncrows = max(0, min(RC, G::CH - strip * RC));
-  float mC[RC];
-  unsigned ownC = 0;
+  // prolongation of q: per plane the z-interpolated coarse window sQ (QW x QH,
+  // origin J0 - 2), then the x-interpolated values sQX at the owned columns;
+  // each thread interpolates in y itself
+  constexpr int NQ = (QW * QH + NT - 1) / NT, NX = NQX / NT;
+  int qoff[NQ];
+  bool qok[NQ];
 #pragma unroll
-  for (int i = 0; i < RC; ++i) {
-    const int y = yA + 2 + strip * RC + i;
-    mC[i] = (inxC && i < ncrows && y >= 1 && y <= n - 1) ? 1.f : 0.f;
-    const int cy = strip * RC + i;
-    if (col >= 1 && col <= OW && cy >= 1 && cy <= OH && mC[i] != 0.f) ownC |= 1u << i;
-  }
-  // x-interpolated coarse values: three (coarse row, B column) entries a thread
-  int qoff[NQX / NT];
-  float qtx[NQX / NT];
-  bool qok[NQX / NT];
-#pragma unroll
-  for (int k = 0; k < NQX / NT; ++k) {
+  for (int k = 0; k < NQ; ++k) {
     const int e = tid + k * NT;
-    const int ky = e / NCOL, c = e % NCOL;
-    const int x = xA + G::BX0 + c, Jy = Jy0 - 2 + ky;
-    const int Ox = min(max(x, 0) / 3, nc - 1);
-    qok[k] = HAS_B && x >= 1 && x <= n - 1 && Jy >= 0 && Jy <= nc;
-    qoff[k] = qok[k] ? Jy * ncp1 + Ox : 0;
-    qtx[k] = (float)(x - 3 * Ox) * (1.f / 3.f);
+    const int Jx = Jx0 - 2 + e % QW, Jy = Jy0 - 2 + e / QW;
+    qok[k] = DOWNP && e < QW * QH && Jx >= 0 && Jx <= nc && Jy >= 0 && Jy <= nc;
+    qoff[k] = qok[k] ? Jy * ncp1 + Jx : 0;
   }
-  float qa[NQX / NT][2], qb[NQX / NT][2];
+  int xq[NX];
+  float xt[NX];
+#pragma unroll
+  for (int k = 0; k < NX; ++k) {
+    const int e = tid + k * NT;
+    const int ky = e / 64, c = e % 64;
+    const int x = xA + 3 + c;
+    const int Ox = min(max(x, 0) / 3, nc - 1);
+    xq[k] = ky * QW + Ox - (Jx0 - 2);
+    xt[k] = (float)(x - 3 * Ox) * (1.f / 3.f);
+  }
+  float qa[NQ], qb[NQ];
   int qOz = -1;
-  // z-interpolated, x-interpolated coarse row values of fine plane s -> sQX[buf]
-  auto make_qx = [&](int s, int buf) {
+  auto make_q = [&](int s, int buf) {  // phase 1: sQ of plane s
     const int Oz = min(max(s, 0) / 3, nc - 1);
     if (Oz != qOz) {
       const float* q0 = p.q + (long long)Oz * ncp1 * ncp1;
       const float* q1 = q0 + ncp1 * ncp1;
 #pragma unroll
-      for (int k = 0; k < NQX / NT; ++k) {
-        qa[k][0] = qok[k] ? q0[qoff[k]] : 0.f;
-        qa[k][1] = qok[k] ? q0[qoff[k] + 1] : 0.f;
-        qb[k][0] = qok[k] ? q1[qoff[k]] : 0.f;
-        qb[k][1] = qok[k] ? q1[qoff[k] + 1] : 0.f;
+      for (int k = 0; k < NQ; ++k) {
+        qa[k] = qok[k] ? q0[qoff[k]] : 0.f;
+        qb[k] = qok[k] ? q1[qoff[k]] : 0.f;
       }
       qOz = Oz;
     }
     const float tz = (float)(s - 3 * Oz) * (1.f / 3.f);
 #pragma unroll
-    for (int k = 0; k < NQX / NT; ++k) {
-      const float v0 = fmaf(tz, qb[k][0] - qa[k][0], qa[k][0]);
-      const float v1 = fmaf(tz, qb[k][1] - qa[k][1], qa[k][1]);
-      sQX[buf * NQX + tid + k * NT] = fmaf(qtx[k], v1 - v0, v0);
+    for (int k = 0; k < NQ; ++k) {
+      const int e = tid + k * NT;
+      if (e < QW * QH) sQ[buf * QW * QH + e] = fmaf(tz, qb[k] - qa[k], qa[k]);
     }
   };
-  if (HAS_B) make_qx(t0 - 1, (t0 - 1) & 1);
+  auto make_qx = [&](int buf) {  // phase 2: sQX from sQ
+    const float* q = sQ + buf * QW * QH;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      const float v0 = q[xq[k]], v1 = q[xq[k] + 1];
+      sQX[buf * NQX + tid + k * NT] = fmaf(xt[k], v1 - v0, v0);
+    }
+  };
+  if (DOWNP) {
+    make_q(t0 - 1, (t0 - 1) & 1);
+    __syncthreads();
+    make_qx((t0 - 1) & 1);
+  }
+  // ---- up-pass geometry: the pair (2 pc, 2 pc + 1) of sR is box columns
+  // 1 + 2 pc (+1) (the owned box + 1 is box columns 2 .. 63); row strip RC + i
+  // is box row 2 + strip RC + i
+  const int xc = xA + 1 + 2 * pc;
+  const float2 mxC = make_float2(xc >= 1 && xc <= n - 1 ? 1.f : 0.f,
+                                 xc + 1 >= 1 && xc + 1 <= n - 1 ? 1.f : 0.f);
+  const int ncrows = max(0, min(RC, CH - strip * RC));
+  float myC[RC];
+#pragma unroll
+  for (int i = 0; i < RC; ++i) {
+    const int y = yA + 2 + strip * RC + i;
+    myC[i] = (i < ncrows && y >= 1 && y <= n - 1) ? 1.f : 0.f;
+  }
 
-  // restriction: one thread per coarse column
-  const bool resT = MODE != SWEEP_DOWNU && tid < NJ;
-  const int cjx = tid % BJX, cjy = tid / BJX;
-  const float a_c = p.a_c, a_f = p.a_f, a_e = p.a_e, a_k = p.a_k, w_invd = p.w_invd;
-  // rolling per-plane parts of the stencils: centre value and W of plane t-1,
-  // Y of planes t-1 and t-2
-  float eB1[RB], WB1[RB], YB1[RB], YB2[RB];
-  float eC1[RC], WC1[RC], YC1[RC], YC2[RC];
+  const float2 ac2 = f2(p.a_c), ae2 = f2(p.a_e), ak2 = f2(p.a_k), w2 = f2(p.w_invd);
+  const float2 neg1 = f2(-1.f);
+  // rolling stencil parts per row: centre of the last plane, PR = W_s + Y_{s-1}
+  // of the last plane s, YR = Y_s
+  float2 eR[RC], PR[RC], YR[RC];
 #pragma unroll
-  for (int i = 0; i < RB; ++i) eB1[i] = WB1[i] = YB1[i] = YB2[i] = 0.f;
-#pragma unroll
-  for (int i = 0; i < RC; ++i) eC1[i] = WC1[i] = YC1[i] = YC2[i] = 0.f;
-  float accR[2] = {0.f, 0.f}, accB[2] = {0.f, 0.f};
+  for (int i = 0; i < RC; ++i) eR[i] = PR[i] = YR[i] = f2(0.f);
+  // restriction accumulators: coarse columns tid and tid + NT, two coarse
+  // planes in flight (by parity)
+  float accR[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, accB[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
@@ -263,8 +320,8 @@ __global__ void __launch_bounds__(NT, 2)
     if (tid == 0 && t + PREF < t1) issue(t + PREF);
     const int k = (t - t0) % NSTAGE;
     if (!mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
-      s_fail = 1;
-      if (atomicCAS(p.fault, 0, 1) == 0) {  // first failure records where
+      s_fail = t - t0 + 1;
+      if (atomicCAS(p.fault, 0, 1) == 0) {  // the first failure records where
         p.fault_info[0] = MODE;
         p.fault_info[1] = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         p.fault_info[2] = t - t0;
@@ -277,177 +334,186 @@ __global__ void __launch_bounds__(NT, 2)
     }
     const float* sE = smem + k * 2 * PLANE_F;
     const float* sRhs = sE + PLANE_F;
-    const int s = t - 1;                                    // stage B plane
-    const int r = FULL ? t - 2 : t;                         // stage C plane
-    // ---- stage B: new e at plane s ----------------------------------------
-    if (HAS_B) {
-      const bool doB = s >= zB0 && s < zB1;
-      const float zm = (s >= 1 && s <= n - 1) ? 1.f : 0.f;
-      const float* E = sE + (strip * RB + G::BX0 - 1) * BOXW + col + G::BX0 - 1;
-      const float* Rh = sRhs + (strip * RB + G::BX0) * BOXW + col + G::BX0;
-      const float* qx = sQX + (s & 1) * NQX;
-      double uo[RB];
-      if (MODE == SWEEP_DOWNU && doB && zm != 0.f) {
+    if (DOWNP) {
+      // ---- down-pass: new e at plane s = t - 1 on the owned box ----------
+      const int s = t - 1;
+      if (pairB) {
+        const bool doB = s >= oz0 && s < oz1 && s >= 1 && s <= n - 1;
+        const float* E = sE + (strip * RB + 2) * BOXW + 2 + 2 * pc;
+        const float* Rh = sRhs + (strip * RB + 3) * BOXW + 3 + 2 * pc;
+        const float* qx = sQX + (s & 1) * NQX;
+        // DOWNU: fetch the FP64 iterate first (its latency overlaps the stencil)
+        double uo[RB][2];
+        if (MODE == SWEEP_DOWNU && doB) {
 #pragma unroll
-        for (int i = 0; i < RB; ++i)
-          if (mB[i] != 0.f)
-            uo[i] = p.u[((long long)s * (n + 1) + yA + G::BX0 + strip * RB + i) * (n + 1) + xb];
-      }
-      float hm = E[0] + E[2], mm = E[1];
-      float hc = E[BOXW] + E[BOXW + 2], mc = E[BOXW + 1];
-#pragma unroll
-      for (int i = 0; i < RB; ++i) {
-        const float* rb = E + (i + 2) * BOXW;
-        const float hb = rb[0] + rb[2], mb = rb[1];
-        const float X = hc + mm + mb;
-        const float Dd = hm + hb;
-        const float W = fmaf(a_c, mc, fmaf(a_f, X, a_e * Dd));
-        const float Y = fmaf(a_f, mc, fmaf(a_e, X, a_k * Dd));
-        if (doB && col < G::BW) {
-          const float Ae = WB1[i] + YB2[i] + Y;
-          const float rho = Rh[i * BOXW] - Ae;
-          const float q0 = qx[qkB[i]], q1 = qx[qkB[i] + NCOL];
-          const float pq = fmaf(tyB[i], q1 - q0, q0);
-          const float ek = zm * mB[i] * (fmaf(w_invd, rho, eB1[i]) + pq);
-          if (FULL) {
-            sB[(strip * RB + i) * 64 + col] = ek;
-          } else if (mB[i] != 0.f && zm != 0.f) {
-            const long long row = (long long)s * (n + 1) + yA + G::BX0 + strip * RB + i;
-            p.u[row * (n + 1) + xb] = uo[i] + (double)ek;
-            p.e_out[s * fplane + (long long)(yA + G::BX0 + strip * RB + i) * ldx + xb] = 0.f;
+          for (int i = 0; i < RB; ++i) {
+            const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
+            uo[i][0] = (myB[i] != 0.f && mxB.x != 0.f) ? p.u[urow + xb] : 0.0;
+            uo[i][1] = (myB[i] != 0.f && mxB.y != 0.f) ? p.u[urow + xb + 1] : 0.0;
           }
         }
-        YB2[i] = YB1[i];
-        YB1[i] = Y;
-        WB1[i] = W;
-        eB1[i] = mc;
-        hm = hc;
-        mm = mc;
-        hc = hb;
-        mc = mb;
+        RowPair up = row_pair(E), ce = row_pair(E + BOXW);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+          const RowPair dn = row_pair(E + (i + 2) * BOXW);
+          const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+          if (doB && myB[i] != 0.f) {
+            const float2 Ae = add2(PR[i], q.Y);
+            const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
+            const float2 rho = fma2(Ae, neg1, rhs);
+            const float2 q0 = ld2(qx + qrB[i]), q1 = ld2(qx + qrB[i] + 64);
+            const float2 pq = fma2(f2(tyB[i]), fma2(q0, neg1, q1), q0);
+            const float2 ek = add2(fma2(w2, rho, eR[i]), pq);
+            float* eo = p.e_out + s * fplane + (long long)(y0 + i) * ldx + xb;
+            if (MODE == SWEEP_DOWN) {
+              if (mxB.x != 0.f) eo[0] = ek.x;
+              if (mxB.y != 0.f) eo[1] = ek.y;
+            } else {
+              const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
+              if (mxB.x != 0.f) {
+                p.u[urow + xb] = uo[i][0] + (double)ek.x;
+                eo[0] = 0.f;
+              }
+              if (mxB.y != 0.f) {
+                p.u[urow + xb + 1] = uo[i][1] + (double)ek.y;
+                eo[1] = 0.f;
+              }
+            }
+          }
+          PR[i] = add2(q.W, YR[i]);
+          YR[i] = q.Y;
+          eR[i] = ce.c;
+          up = ce;
+          ce = dn;
+        }
       }
+      if (t + 1 < t1) {
+        make_q(s + 1, (s + 1) & 1);
+        __syncthreads();
+        make_qx((s + 1) & 1);
+      }
+      continue;
     }
-    // ---- stage C: residual of the new e at plane r --------------------------
-    if (FULL) {
-      __syncthreads();
-      if (col < G::CW && s >= zB0) {
-        const bool doC = r >= zC0 && r < zC1;
-        const float zm = (r >= 1 && r <= n - 1) ? 1.f : 0.f;
-        // owned planes of the last chunk run past the domain: store interior only
-        const bool ownZ = r >= oz0 && r < oz1 && r >= 1 && r <= n - 1;
-        // rhs of plane r is in the previous slot
-        const float* sRhsPrev = smem + ((t - 1 - t0 + NSTAGE) % NSTAGE) * 2 * PLANE_F + PLANE_F;
-        const float* Rh = sRhsPrev + (strip * RC + 2) * BOXW + col + 2;
-        const float* Bp = sB + (strip * RC) * 64 + col;
-        float* eo = p.e_out + (long long)r * fplane + (long long)(yA + 2 + strip * RC) * ldx + xc;
-        float hm = Bp[0] + Bp[2], mm = Bp[1];
-        float hc = Bp[64] + Bp[66], mc = Bp[65];
+    // ---- up-pass: residual of plane r ---------------------------------------
+    const int r = MODE == SWEEP_UPE ? t - 1 : t;
+    const bool doC = r >= zC0 && r < zC1;
+    const float* wbase;
+    int pitch;
+    if (MODE == SWEEP_UPE) {
+      const float zm = (r >= 1 && r <= n - 1) ? 1.f : 0.f;
+      const float* E = sE + (strip * RC + 1) * BOXW + 2 * pc;
+      const float* Rh = sRhs + (strip * RC + 2) * BOXW + 1 + 2 * pc;
+      RowPair up = row_pair(E), ce = row_pair(E + BOXW);
 #pragma unroll
-        for (int i = 0; i < RC; ++i) {
-          if (i >= ncrows) break;
-          const float* rb = Bp + (i + 2) * 64;
-          const float hb = rb[0] + rb[2], mb = rb[1];
-          const float X = hc + mm + mb;
-          const float Dd = hm + hb;
-          const float W = fmaf(a_c, mc, fmaf(a_f, X, a_e * Dd));
-          const float Y = fmaf(a_f, mc, fmaf(a_e, X, a_k * Dd));
-          if (doC) {
-            const float Ae = WC1[i] + YC2[i] + Y;
-            const float rho = zm * mC[i] * (Rh[i * BOXW] - Ae);
-            if (ownZ && ((ownC >> i) & 1u)) eo[(long long)i * ldx] = eC1[i];
-            sR[(strip * RC + i) * 62 + col] = rho;
-          }
-          YC2[i] = YC1[i];
-          YC1[i] = Y;
-          WC1[i] = W;
-          eC1[i] = mc;
-          hm = hc;
-          mm = mc;
-          hc = hb;
-          mc = mb;
+      for (int i = 0; i < RC; ++i) {
+        if (i >= ncrows) break;
+        const RowPair dn = row_pair(E + (i + 2) * BOXW);
+        const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+        if (doC) {
+          const float2 Ae = add2(PR[i], q.Y);
+          const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
+          const float2 rho = mul2(fma2(Ae, neg1, rhs), mul2(mxC, f2(zm * myC[i])));
+          st2(sR + (strip * RC + i) * SR_P + 2 * pc, rho);
         }
+        PR[i] = add2(q.W, YR[i]);
+        YR[i] = q.Y;
+        up = ce;
+        ce = dn;
       }
       __syncthreads();
+      // sR column j is box column j + 1, row j box row j + 2
+      wbase = sR;
+      pitch = SR_P;
+    } else {
+      // UP: rho = rhs (zero outside the interior), read from the staged box
+      wbase = sRhs + 2 * BOXW + 1;
+      pitch = BOXW;
     }
     // ---- restriction and damping right-hand side of plane r -----------------
-    if (resT && r >= zC0 && r < zC1) {
-      // the 5x5 window of the coarse column, summed per class of distances
-      // (|ox|, |oy|) from its centre: (0,0) (1,0) (2,0) (1,1) (1,2) (2,2)
-      const float* w0;
-      int pitch;
-      if (FULL) {
-        w0 = sR + (3 * cjy) * 62 + 3 * cjx;
-        pitch = 62;
-      } else {
-        w0 = sRhs + (3 * cjy + 2) * BOXW + 3 * cjx + 2;
-        pitch = BOXW;
-      }
-      float c0 = 0.f, l1 = 0.f, l2 = 0.f, p11 = 0.f, p12 = 0.f, p22 = 0.f;
+    if (doC) {
 #pragma unroll
-      for (int oy = 0; oy < 5; ++oy) {
-        const float* row = w0 + oy * pitch;
-        const float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
-        if (oy == 2) {
-          c0 = v2;
-          l1 += v1 + v3;
-          l2 += v0 + v4;
-        } else if (oy == 1 || oy == 3) {
-          l1 += v2;
-          p11 += v1 + v3;
-          p12 += v0 + v4;
-        } else {
-          l2 += v2;
-          p12 += v1 + v3;
-          p22 += v0 + v4;
-        }
-      }
-      const float rin = c0 + (2.f / 3.f) * l1 + (1.f / 3.f) * l2 + (4.f / 9.f) * p11 +
-                        (2.f / 9.f) * p12 + (1.f / 9.f) * p22;
-      const int jtop = (r + 2) / 3;  // r >= -2
+      for (int pass = 0; pass < 2; ++pass) {
+        const int cj = tid + pass * NT;
+        if (cj >= NJ) break;
+        const int cjx = cj % BJX, cjy = cj / BJX;
+        // the 5x5 window of the coarse column (box columns 3 cjx + 2 .. + 6,
+        // rows 3 cjy + 2 .. + 6), summed per class of distances (|ox|, |oy|)
+        // from its centre: (0,0) (1,0) (2,0) (1,1) (1,2) (2,2)
+        const float* w0 = wbase + (3 * cjy) * pitch + 3 * cjx + 1;
+        float c0 = 0.f, l1 = 0.f, l2 = 0.f, p11 = 0.f, p12 = 0.f, p22 = 0.f;
 #pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const int Jz = jtop - 1 + d;
-        const int oz = r - 3 * Jz;
-        if (oz < -2 || oz > 2 || Jz < Jz0 || Jz >= Jz1) continue;
-        const int az = oz < 0 ? -oz : oz;
-        const int slot = Jz & 1;
-        if (oz == -2) {
-          accR[slot] = 0.f;
-          accB[slot] = 0.f;
+        for (int oy = 0; oy < 5; ++oy) {
+          const float* row = w0 + oy * pitch;
+          const float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
+          if (oy == 2) {
+            c0 = v2;
+            l1 += v1 + v3;
+            l2 += v0 + v4;
+          } else if (oy == 1 || oy == 3) {
+            l1 += v2;
+            p11 += v1 + v3;
+            p12 += v0 + v4;
+          } else {
+            l2 += v2;
+            p12 += v1 + v3;
+            p22 += v0 + v4;
+          }
         }
-        // d-linear restriction: weight (1 - |o|/3) per direction
-        accR[slot] = fmaf(1.f - (float)az * (1.f / 3.f), rin, accR[slot]);
-        const float* dz = p.dcls + 6 * az;
-        accB[slot] += dz[0] * c0 + dz[1] * l1 + dz[2] * l2 + dz[3] * p11 + dz[4] * p12 +
-                      dz[5] * p22;
-        if (oz == 2) {
-          const int Jx = Jx0 + cjx, Jy = Jy0 + cjy;
-          if (Jx >= 1 && Jx <= nc - 1 && Jy >= 1 && Jy <= nc - 1 && Jz >= 1 && Jz <= nc - 1) {
-            const float rc = accR[slot];
-            const float bt = p.omega * accB[slot];
-            const long long ci = ((long long)Jz * ncp1 + Jy) * ncp1 + Jx;
-            p.r_c[ci] = rc;
-            if (p.variant == V_JAC) {
-              p.bt_c[ci] = bt;
-              p.g_c[ci] = p.c_invd * (p.omega * rc - p.omega_t * bt);
-            } else {
-              p.bt_c[ci] = 0.f;
-              p.g_c[ci] = p.gscale * p.omega * p.c_invd * rc;
+        const float rin = c0 + (2.f / 3.f) * l1 + (1.f / 3.f) * l2 + (4.f / 9.f) * p11 +
+                          (2.f / 9.f) * p12 + (1.f / 9.f) * p22;
+        const int jtop = (r + 2) / 3;  // r >= -2
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          const int Jz = jtop - 1 + d;
+          const int oz = r - 3 * Jz;
+          if (oz < -2 || oz > 2 || Jz < Jz0 || Jz >= Jz1) continue;
+          const int az = oz < 0 ? -oz : oz;
+          const int slot = Jz & 1;
+          float aR = slot ? accR[pass][1] : accR[pass][0];
+          float aB = slot ? accB[pass][1] : accB[pass][0];
+          if (oz == -2) aR = aB = 0.f;
+          // d-linear restriction: weight (1 - |o|/3) per direction
+          aR = fmaf(1.f - (float)az * (1.f / 3.f), rin, aR);
+          const float* dz = p.dcls + 6 * az;
+          aB += dz[0] * c0 + dz[1] * l1 + dz[2] * l2 + dz[3] * p11 + dz[4] * p12 + dz[5] * p22;
+          if (slot) {
+            accR[pass][1] = aR;
+            accB[pass][1] = aB;
+          } else {
+            accR[pass][0] = aR;
+            accB[pass][0] = aB;
+          }
+          if (oz == 2) {
+            const int Jx = Jx0 + cjx, Jy = Jy0 + cjy;
+            if (Jx >= 1 && Jx <= nc - 1 && Jy >= 1 && Jy <= nc - 1 && Jz >= 1 &&
+                Jz <= nc - 1) {
+              const float bt = p.omega * aB;
+              const long long ci = ((long long)Jz * ncp1 + Jy) * ncp1 + Jx;
+              p.r_c[ci] = aR;
+              if (p.variant == V_JAC) {
+                p.bt_c[ci] = bt;
+                p.g_c[ci] = p.c_invd * (p.omega * aR - p.omega_t * bt);
+              } else {
+                p.bt_c[ci] = 0.f;
+                p.g_c[ci] = p.gscale * p.omega * p.c_invd * aR;
+              }
             }
           }
         }
       }
     }
-    // ---- coarse values for the next stage-B plane ---------------------------
-    if (HAS_B && t + 1 < t1) make_qx(s + 1, (s + 1) & 1);
   }
   __syncthreads();
   if (s_fail && tid == 0) {
     atomicExch(p.fault, 1);
-    // let the copies still in flight land before the block's memory is reused
-    for (int k = 0; k < NSTAGE; ++k) {
-      for (long i = 0; i < kWaitLimit / 64; ++i)
-        if (mbar_try(bar0 + 8 * k, 0) || mbar_try(bar0 + 8 * k, 1)) break;
+    // let the copies still in flight (steps tf .. tf + PREF) land before the
+    // block's shared memory is released
+    const int tf = t0 + s_fail - 1;
+    for (int tt = tf; tt <= tf + PREF && tt < t1; ++tt) {
+      const uint32_t bar = bar0 + 8 * ((tt - t0) % NSTAGE);
+      const uint32_t par = ((tt - t0) / NSTAGE) & 1;
+      for (long i = 0; i < kWaitLimit / 16 && !mbar_try(bar, par); ++i) {
+      }
     }
   }
 }
@@ -549,12 +615,15 @@ void sweep3_grid(int nc, int zc, dim3* grid) {
 }
 
 bool sweep3_prepare() {
-  return cudaFuncSetAttribute(k_sweep3<SWEEP_FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SMEM_BYTES) == cudaSuccess &&
-         cudaFuncSetAttribute(k_sweep3<SWEEP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SMEM_BYTES) == cudaSuccess &&
+  const int bytes = (int)SMEM_BYTES;
+  return cudaFuncSetAttribute(k_sweep3<SWEEP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k_sweep3<SWEEP_UPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k_sweep3<SWEEP_DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes) == cudaSuccess &&
          cudaFuncSetAttribute(k_sweep3<SWEEP_DOWNU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SMEM_BYTES) == cudaSuccess;
+                              bytes) == cudaSuccess;
 }
 
 template <int MODE>
@@ -566,12 +635,12 @@ static void launch_mode(const Sweep3Params& p, const Sweep3Maps& maps, int ein, 
 
 void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
                    cudaStream_t s) {
-  if (mode == SWEEP_FULL)
-    launch_mode<SWEEP_FULL>(p, maps, ein, s);
-  else if (mode == SWEEP_UP)
-    launch_mode<SWEEP_UP>(p, maps, ein, s);
-  else
-    launch_mode<SWEEP_DOWNU>(p, maps, ein, s);
+  switch (mode) {
+    case SWEEP_UP: launch_mode<SWEEP_UP>(p, maps, ein, s); break;
+    case SWEEP_UPE: launch_mode<SWEEP_UPE>(p, maps, ein, s); break;
+    case SWEEP_DOWN: launch_mode<SWEEP_DOWN>(p, maps, ein, s); break;
+    default: launch_mode<SWEEP_DOWNU>(p, maps, ein, s); break;
+  }
 }
 
 int refine3_blocks(int n, int zc) {

@@ -1,4 +1,4 @@
-// Parameters of the fused 3-D sweeps (uniform finest operator, d-linear
+// Parameters of the 3-D fine-level sweeps (uniform finest operator, d-linear
 // transfers) and of the z-marching FP64 refinement residual.
 #pragma once
 
@@ -8,7 +8,9 @@
 
 namespace adafac {
 
-enum SweepMode { SWEEP_UP = 0, SWEEP_FULL = 1, SWEEP_DOWNU = 2 };
+// UP: first up-pass of a refinement step (e = 0); UPE: up-pass of e;
+// DOWN: down-pass; DOWNU: last down-pass (u += e, the other buffer zeroed)
+enum SweepMode { SWEEP_UP = 0, SWEEP_UPE = 1, SWEEP_DOWN = 2, SWEEP_DOWNU = 3 };
 
 // coarse columns per block (x, y); the z extent is a launch parameter
 constexpr int kSweepBJX = 20, kSweepBJY = 8;
@@ -21,7 +23,7 @@ struct Sweep3Params {
   // uniform stencil: A e = a_c e + a_f (6 faces) + a_e (12 edges) + a_k (8 corners)
   float a_c = 0, a_f = 0, a_e = 0, a_k = 0;
   float w_invd = 0;                // omega / diag(A_L)
-  float* e_out = nullptr;          // FULL: new correction; DOWNU: zeroed
+  float* e_out = nullptr;          // DOWN: new correction; DOWNU: zeroed
   const float* q = nullptr;        // level L-1 vector to prolong
   float* r_c = nullptr;            // level L-1 restricted residual
   float* bt_c = nullptr;           // level L-1 damping right-hand side
