@@ -78,6 +78,13 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # the first query initialises NVML, which can stall the GPU: wait for
+        # the first sample before the timed region starts
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 10.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
         time.sleep(0.3)
 
     def stop(self):
@@ -185,13 +192,24 @@ def bench_reference(args, w):
     print(json.dumps(out), flush=True)
 
 
+L2_BYTES = 126 * 2 ** 20
+
+
+def _needs_flush(w, precision):
+    """Flush L2 between steps unless the fine-level arrays a step touches
+    (u, b in FP64; mixed: two FP32 corrections and the FP32 right-hand side)
+    exceed twice the L2 size."""
+    per = 8 + 8 + (4 + 4 + 4 if precision == "mixed" else 8 + 8)
+    return (3 ** w.depth + 1) ** w.dim * per < 2 * L2_BYTES
+
+
 def _config(w, args, cycles):
     return {"workload": w.name, "dim": w.dim, "depth": w.depth,
             "fine_dofs": (3 ** w.depth - 1) ** w.dim, "dofs_all_levels": sum(w.level_dofs()),
             "precision": args.precision, "variant": "adAFAC-Jac", "transfer": w.transfer,
             "rtilde": "truncated", "tol": args.tol, "cycles_per_step": cycles,
-            "l2": "inputs larger than L2" if sum(w.level_dofs()) * 12 > 130e6
-                  else "L2 flushed between steps",
+            "l2": "L2 flushed between steps" if _needs_flush(w, args.precision)
+                  else "working set of a step larger than L2",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -223,9 +241,8 @@ def bench_ours(args, w):
             cycles = c
         assert c == cycles, "cycle count of the solve must be reproducible"
     flush = None
-    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
-    small = upd_cycle * 12 < 2 * l2_bytes
-    if small:
+    if _needs_flush(w, args.precision):
+        l2_bytes = max(L2_BYTES, torch.cuda.get_device_properties(dev).L2_cache_size)
         flush = torch.empty(4 * l2_bytes // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 

@@ -96,7 +96,7 @@ typedef struct {
 enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1 };
 
 /* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,
- * inner_cycles 12, omega = omega_tilde = 0.6, omega_exp = 0.5, path AUTO. */
+ * inner_cycles 24, omega = omega_tilde = 0.6, omega_exp = 0.5, path AUTO. */
 adafac_status adafac_default_options(adafac_options* opt);
 
 /* Device bytes a handle for (tree, opt) needs.  Pass at least this much

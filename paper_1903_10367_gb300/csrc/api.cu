@@ -92,6 +92,7 @@ struct adafac_handle_s {
   bool fast3 = false;
   float* e32b = nullptr;     // second correction buffer (ping-pong)
   int ebase = 0;             // which of e32 / e32b holds zeros at a step start
+  long long e_elems = 0;     // floats of e32 / e32b / rhs32 (padded rows on the 3-D path)
   int npartials = 0;
   int ldx = 0;               // row stride of the padded FP32 fine arrays
   Sweep3Maps maps;
@@ -239,6 +240,7 @@ void carve(adafac_handle h, Carver& cv) {
     const long long np1 = h->lev[L].n + 1;
     h->ldx = h->fast3 ? (int)((np1 + 3) / 4 * 4) : (int)np1;
     const long long Vp = h->fast3 ? (long long)h->ldx * np1 * np1 : Vf;
+    h->e_elems = Vp;
     h->e32 = cv.take<float>(Vp);
     h->rhs32 = cv.take<float>(Vp);
     if (h->fast3) h->e32b = cv.take<float>(Vp);
@@ -421,7 +423,7 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
       v.boxmg = a.boxmg;
       v.P = lv.P32;
     }
-    cudaMemsetAsync(h->e32, 0, sizeof(float) * (size_t)h->ldx * (fine.n + 1) * (fine.n + 1), s);
+    cudaMemsetAsync(h->e32, 0, sizeof(float) * (size_t)h->e_elems, s);
   }
   if (h->fast3) {
     // stencil classes of the uniform 27-point operator: centre, face, edge, corner
@@ -823,8 +825,7 @@ __global__ void k_mask_boundary3(double* u, int n) {
 
 adafac_status reset_control(adafac_handle h) {
   launch_reset_control(h->ctl, h->stream);
-  const long long np1 = h->lev[h->L].n + 1;
-  const size_t ebytes = sizeof(float) * (size_t)(h->ldx ? h->ldx : np1) * np1 * np1;
+  const size_t ebytes = sizeof(float) * (size_t)h->e_elems;
   if (h->e32) cudaMemsetAsync(h->e32, 0, ebytes, h->stream);
   if (h->e32b) cudaMemsetAsync(h->e32b, 0, ebytes, h->stream);
   h->ebase = 0;
@@ -842,7 +843,7 @@ adafac_status adafac_default_options(adafac_options* o) {
   o->precision = ADAFAC_PRECISION_FP64;
   o->rtilde = ADAFAC_RTILDE_TRUNCATED;
   o->form = ADAFAC_FORM_CS;
-  o->inner_cycles = 12;
+  o->inner_cycles = 24;
   o->omega = 0.6;
   o->omega_tilde = 0.6;
   o->omega_exp = 0.5;

@@ -55,26 +55,40 @@ __global__ void k_residual(LevelView<T> lv, const TX* __restrict__ x, const TX* 
 //   g_c = M_c^-1 (omega r_c - omega~ b~_c)  (c_l - c~_l, Eq. 9)  [JAC]
 //       = gscale omega M_c^-1 r_c                        [ADDITIVE/EXP/PI]
 template <int D, typename T>
-__global__ void k_restrict(LevelView<T> lf, LevelView<T> lc, CycleParams<T> cp,
-                           const T* __restrict__ r_f, const T* __restrict__ y_f,
-                           T* __restrict__ r_c, int rc_given, T* __restrict__ bt_c,
-                           T* __restrict__ g_c, T gscale, const Control* ctl) {
+__global__ void __launch_bounds__(256) k_restrict(LevelView<T> lf, LevelView<T> lc,
+                                                  CycleParams<T> cp, const T* __restrict__ r_f,
+                                                  const T* __restrict__ y_f, T* __restrict__ r_c,
+                                                  int rc_given, T* __restrict__ bt_c,
+                                                  T* __restrict__ g_c, T gscale,
+                                                  const Control* ctl) {
   if (halted(ctl)) return;
   constexpr int N5 = ipow_c(5, D);
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < lc.V;
-       v += (long long)gridDim.x * blockDim.x) {
+  constexpr int PER = (N5 + 31) / 32;  // window points per lane
+  // one warp per coarse vertex: lane l takes the window points l, l + 32, ...
+  __shared__ T s_st[N5];
+  for (int k = threadIdx.x; k < N5; k += blockDim.x) s_st[k] = cp.stilde[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long v = w0; v < lc.V; v += nw) {
     int J[D];
     decode<D>(v, lc.np1, J);
     if (!is_interior<D>(J, lc.n)) {
-      if (!rc_given) r_c[v] = T(0);
-      if (bt_c) bt_c[v] = T(0);
-      g_c[v] = T(0);
+      if (lane == 0) {
+        if (!rc_given) r_c[v] = T(0);
+        if (bt_c) bt_c[v] = T(0);
+        g_c[v] = T(0);
+      }
       continue;
     }
     T rc = T(0), bt = T(0);
-    for (int k = 0; k < N5; ++k) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int k = lane + 32 * i;
+      if (k >= N5) break;
       int fc[D], t = k;
-      int sidx = k;
+#pragma unroll
       for (int j = 0; j < D; ++j) {
         fc[j] = 3 * J[j] + (t % 5) - 2;
         t /= 5;
@@ -87,9 +101,15 @@ __global__ void k_restrict(LevelView<T> lf, LevelView<T> lc, CycleParams<T> cp,
         if (cp.rtilde_exact)
           bt += w * y_f[fv];
         else
-          bt += cp.stilde[sidx] * rv;
+          bt += s_st[k] * rv;
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rc += __shfl_xor_sync(0xffffffffu, rc, o);
+      bt += __shfl_xor_sync(0xffffffffu, bt, o);
+    }
+    if (lane != 0) continue;
     if (rc_given) rc = r_c[v];
     else r_c[v] = rc;
     const T id = inv_diag(lc, v);
@@ -393,8 +413,9 @@ template <int D, typename T>
 void launch_restrict(const LevelView<T>& lf, const LevelView<T>& lc, const CycleParams<T>& cp,
                      const T* r_f, const T* y_f, T* r_c, int rc_given, T* bt_c, T* g_c,
                      T gscale, const Control* ctl, cudaStream_t s) {
-  k_restrict<D, T><<<grid_for(lc.V, kT, kCap), kT, 0, s>>>(lf, lc, cp, r_f, y_f, r_c, rc_given,
-                                                          bt_c, g_c, gscale, ctl);
+  // one warp per coarse vertex
+  k_restrict<D, T><<<grid_for(lc.V * 32, kT, kCap), kT, 0, s>>>(lf, lc, cp, r_f, y_f, r_c,
+                                                               rc_given, bt_c, g_c, gscale, ctl);
 }
 
 template <int D, typename T>

@@ -519,20 +519,27 @@ __global__ void __launch_bounds__(NT, 3)
 }
 
 // FP64 residual of a uniform 3-D operator, z-marching with in-plane sums:
-// rhs32 = (float)(b - A u) and per-block sums of h^3 r^2.
+// rhs32 = (float)(b - A u) and per-block sums of h^3 r^2.  With the face
+// coefficient zero (the d-linear element in 3-D), per plane p
+//   W_p = a_c u + a_e D_p,  Y_p = a_e X_p + a_k D_p,
+// X_p / D_p the sums of the 4 in-plane face / diagonal neighbours, and
+// (A u)_s = W_s + Y_{s-1} + Y_{s+1}: 14 FP64 operations per vertex, the
+// bound of this kernel on a GPU with few FP64 units.
 constexpr int RT_X = 32, RT_Y = 8;
 
 __global__ void __launch_bounds__(RT_X* RT_Y) k_refine3(const Refine3Params p) {
   if (halted(p.ctl)) return;
   __shared__ double sU[(RT_X + 2) * (RT_Y + 2)];
-  __shared__ double red[RT_X * RT_Y];
+  __shared__ double red[RT_X * RT_Y / 32];
   const int n = p.n, np1 = n + 1;
   const int tx = threadIdx.x % RT_X, ty = threadIdx.x / RT_X;
   const int x = blockIdx.x * RT_X + tx, y = blockIdx.y * RT_Y + ty;
   const int zlo = blockIdx.z * p.zc + 1;
   const int zhi = min(zlo + p.zc, n);            // planes [zlo, zhi)
+  const bool inner = x >= 1 && x <= n - 1 && y >= 1 && y <= n - 1;
   constexpr int W = RT_X + 2;
-  double Xs[3] = {0, 0, 0}, Ds[3] = {0, 0, 0}, Cs[3] = {0, 0, 0};
+  const double ac = p.a_c, ae = p.a_e, ak = p.a_k;
+  double Wm = 0.0, Ym = 0.0, Ymm = 0.0;          // W_{z-1}, Y_{z-1}, Y_{z-2}
   double acc = 0.0;
   for (int z = zlo - 1; z <= zhi; ++z) {
     for (int i = threadIdx.x; i < W * (RT_Y + 2); i += RT_X * RT_Y) {
@@ -544,35 +551,32 @@ __global__ void __launch_bounds__(RT_X* RT_Y) k_refine3(const Refine3Params p) {
     }
     __syncthreads();
     const int ai = (ty + 1) * W + tx + 1;
-    Xs[0] = Xs[1];
-    Xs[1] = Xs[2];
-    Xs[2] = sU[ai - 1] + sU[ai + 1] + sU[ai - W] + sU[ai + W];
-    Ds[0] = Ds[1];
-    Ds[1] = Ds[2];
-    Ds[2] = sU[ai - W - 1] + sU[ai - W + 1] + sU[ai + W - 1] + sU[ai + W + 1];
-    Cs[0] = Cs[1];
-    Cs[1] = Cs[2];
-    Cs[2] = sU[ai];
+    const double X = (sU[ai - 1] + sU[ai + 1]) + (sU[ai - W] + sU[ai + W]);
+    const double D = (sU[ai - W - 1] + sU[ai - W + 1]) + (sU[ai + W - 1] + sU[ai + W + 1]);
+    const double Wz = fma(ae, D, ac * sU[ai]);
+    const double Yz = fma(ae, X, ak * D);
     __syncthreads();
     const int zz = z - 1;  // residual plane
-    if (zz >= zlo && zz < zhi && x >= 1 && x <= n - 1 && y >= 1 && y <= n - 1) {
-      const double Au = p.a_c * Cs[1] + p.a_f * (Xs[1] + Cs[0] + Cs[2]) +
-                        p.a_e * (Ds[1] + Xs[0] + Xs[2]) + p.a_k * (Ds[0] + Ds[2]);
+    if (zz >= zlo && zz < zhi && inner) {
       const long long gi = ((long long)zz * np1 + y) * np1 + x;
-      const double r = p.b[gi] - Au;
+      const double r = ((p.b[gi] - Wm) - Ymm) - Yz;
       p.rhs32[((long long)zz * np1 + y) * p.ldx + x] = (float)r;
-      acc += r * r;
+      acc = fma(r, r, acc);
     }
+    Ymm = Ym;
+    Ym = Yz;
+    Wm = Wz;
   }
-  red[threadIdx.x] = acc * p.hD;
+  // block sum: warp shuffles, then the warps' partial sums
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = acc;
   __syncthreads();
-  for (int w = RT_X * RT_Y / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < RT_X * RT_Y / 32; ++w) t += red[w];
     const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    p.partials[b] = red[0];
+    p.partials[b] = t * p.hD;
   }
 }
 
