@@ -365,13 +365,30 @@ def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch):
             "includes": "setup (H2D copies, BoxMG/Galerkin), solve to tol, D2H of u"}
 
 
+def kernel_source_hash():
+    """Fingerprint of the CUDA sources: DRAM counters taken on another build
+    of the kernels do not describe this one."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1903_10367_gb300", "csrc")
+    h = hashlib.sha256()
+    for ext in (".cu", ".cuh", ".h"):
+        for name in sorted(os.listdir(csrc)):
+            if name.endswith(ext):
+                with open(os.path.join(csrc, name), "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_from_profile(kind, w):
-    """DRAM bytes per launch of this kernel from the committed ncu summary, if
-    one exists for the current kernel build (profiles/traffic.json)."""
+    """DRAM bytes (read + write) per launch of this kernel from the committed
+    ncu summary (profiles/traffic.json), or None when the summary was taken on
+    other kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             table = json.load(fh)
+        if table.get("source_hash") != kernel_source_hash():
+            return None
         return table.get(w.name, {}).get(kind)
     except Exception:
         return None

@@ -38,25 +38,21 @@ namespace adafac {
 
 namespace {
 
-constexpr int NT = 128;                     // threads: 32 column pairs x 4 strips
 constexpr int BJX = kSweepBJX, BJY = kSweepBJY;
 constexpr int OW = 3 * BJX, OH = 3 * BJY;   // owned fine box (x, y): 60 x 24
 constexpr int NPAIR = 32;                   // thread column pairs
-constexpr int NSTRIP = NT / NPAIR;          // thread row strips
 constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane: 68 x 30
 constexpr int PLANE_F = 2048;               // floats per staged plane (128-byte multiple)
 constexpr int NSTAGE = 4, PREF = 3;         // ring slots, planes staged ahead
 constexpr int QW = BJX + 4, QH = BJY + 4;   // coarse q window, origin (J0x - 2, J0y - 2)
 constexpr int NQX = QH * 64;                // x-interpolated coarse values per plane
 constexpr int NJ = BJX * BJY;               // coarse columns of a block
-constexpr int RB = OH / NSTRIP;             // down-pass rows per strip
-constexpr int CH = OH + 2, RC = (CH + NSTRIP - 1) / NSTRIP;  // up-pass rows, per strip
+constexpr int CH = OH + 2;                  // up-pass rows (owned box + 1)
 constexpr int SR_P = 64;                    // pitch of the up-pass residual plane
 constexpr long kWaitLimit = 1L << 24;       // polls before a wait gives up
 static_assert(BOXW * BOXH <= PLANE_F, "staged box fits its slot");
 static_assert((BOXW * 4) % 16 == 0, "box rows are 16-byte multiples");
-static_assert(OW == 2 * (NPAIR - 2) && OH % NSTRIP == 0, "thread tiling of the owned box");
-static_assert(NJ <= 2 * NT && NQX % NT == 0, "thread counts");
+static_assert(OW == 2 * (NPAIR - 2), "thread tiling of the owned box");
 // the slot refilled at step t (that of t + PREF) was last read at step
 // t + PREF - NSTAGE <= t - 1, before the block barrier that opens step t
 static_assert(PREF < NSTAGE, "prefetch distance");
@@ -149,11 +145,18 @@ __device__ __forceinline__ Parts parts(const RowPair& up, const RowPair& ce, con
   return q;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NT, 3)
+// NT threads: 32 column pairs x NT/32 row strips; MINB blocks per SM
+template <int MODE, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_sweep3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
              const __grid_constant__ CUtensorMap tm_rhs) {
   constexpr bool DOWNP = MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU;
+  constexpr int NSTRIP = NT / NPAIR;
+  constexpr int RB = OH / NSTRIP;                        // down-pass rows per strip
+  constexpr int RCB = CH / NSTRIP, RCX = CH % NSTRIP;    // up-pass rows per strip:
+  constexpr int RC = RCB + (RCX ? 1 : 0);                // RCB + 1 for the first RCX
+  constexpr int NPASS = (NJ + NT - 1) / NT;              // restriction passes
+  static_assert(OH % NSTRIP == 0 && NQX % NT == 0, "thread tiling");
   constexpr bool LOAD_E = MODE != SWEEP_UP;
   extern __shared__ __align__(128) float smem[];
   __shared__ int s_fail;
@@ -295,11 +298,12 @@ __global__ void __launch_bounds__(NT, 3)
   const int xc = xA + 1 + 2 * pc;
   const float2 mxC = make_float2(xc >= 1 && xc <= n - 1 ? 1.f : 0.f,
                                  xc + 1 >= 1 && xc + 1 <= n - 1 ? 1.f : 0.f);
-  const int ncrows = max(0, min(RC, CH - strip * RC));
+  const int rc0 = strip * RCB + min(strip, RCX);           // first up-pass row
+  const int ncrows = RCB + (strip < RCX ? 1 : 0);
   float myC[RC];
 #pragma unroll
   for (int i = 0; i < RC; ++i) {
-    const int y = yA + 2 + strip * RC + i;
+    const int y = yA + 2 + rc0 + i;
     myC[i] = (i < ncrows && y >= 1 && y <= n - 1) ? 1.f : 0.f;
   }
 
@@ -310,9 +314,11 @@ __global__ void __launch_bounds__(NT, 3)
   float2 eR[RC], PR[RC], YR[RC];
 #pragma unroll
   for (int i = 0; i < RC; ++i) eR[i] = PR[i] = YR[i] = f2(0.f);
-  // restriction accumulators: coarse columns tid and tid + NT, two coarse
+  // restriction accumulators: coarse columns tid, tid + NT, ..., two coarse
   // planes in flight (by parity)
-  float accR[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, accB[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  float accR[NPASS][2], accB[NPASS][2];
+#pragma unroll
+  for (int i = 0; i < NPASS; ++i) accR[i][0] = accR[i][1] = accB[i][0] = accB[i][1] = 0.f;
 
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
@@ -401,8 +407,8 @@ __global__ void __launch_bounds__(NT, 3)
     int pitch;
     if (MODE == SWEEP_UPE) {
       const float zm = (r >= 1 && r <= n - 1) ? 1.f : 0.f;
-      const float* E = sE + (strip * RC + 1) * BOXW + 2 * pc;
-      const float* Rh = sRhs + (strip * RC + 2) * BOXW + 1 + 2 * pc;
+      const float* E = sE + (rc0 + 1) * BOXW + 2 * pc;
+      const float* Rh = sRhs + (rc0 + 2) * BOXW + 1 + 2 * pc;
       RowPair up = row_pair(E), ce = row_pair(E + BOXW);
 #pragma unroll
       for (int i = 0; i < RC; ++i) {
@@ -413,7 +419,7 @@ __global__ void __launch_bounds__(NT, 3)
           const float2 Ae = add2(PR[i], q.Y);
           const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
           const float2 rho = mul2(fma2(Ae, neg1, rhs), mul2(mxC, f2(zm * myC[i])));
-          st2(sR + (strip * RC + i) * SR_P + 2 * pc, rho);
+          st2(sR + (rc0 + i) * SR_P + 2 * pc, rho);
         }
         PR[i] = add2(q.W, YR[i]);
         YR[i] = q.Y;
@@ -432,7 +438,7 @@ __global__ void __launch_bounds__(NT, 3)
     // ---- restriction and damping right-hand side of plane r -----------------
     if (doC) {
 #pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
+      for (int pass = 0; pass < NPASS; ++pass) {
         const int cj = tid + pass * NT;
         if (cj >= NJ) break;
         const int cjx = cj % BJX, cjy = cj / BJX;
@@ -618,23 +624,45 @@ void sweep3_grid(int nc, int zc, dim3* grid) {
   *grid = dim3((ncp1 + BJX - 1) / BJX, (ncp1 + BJY - 1) / BJY, (ncp1 + zc - 1) / zc);
 }
 
+// threads and blocks per SM of each mode
+template <int MODE>
+struct Shape;
+template <>
+struct Shape<SWEEP_UP> {
+  static constexpr int NT = 256, MINB = 3;
+};
+template <>
+struct Shape<SWEEP_UPE> {
+  static constexpr int NT = 256, MINB = 3;
+};
+template <>
+struct Shape<SWEEP_DOWN> {
+  static constexpr int NT = 128, MINB = 3;
+};
+template <>
+struct Shape<SWEEP_DOWNU> {
+  static constexpr int NT = 128, MINB = 3;
+};
+
+template <int MODE>
+static bool prepare_mode() {
+  using S = Shape<MODE>;
+  return cudaFuncSetAttribute(k_sweep3<MODE, S::NT, S::MINB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SMEM_BYTES) == cudaSuccess;
+}
+
 bool sweep3_prepare() {
-  const int bytes = (int)SMEM_BYTES;
-  return cudaFuncSetAttribute(k_sweep3<SWEEP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes) == cudaSuccess &&
-         cudaFuncSetAttribute(k_sweep3<SWEEP_UPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes) == cudaSuccess &&
-         cudaFuncSetAttribute(k_sweep3<SWEEP_DOWN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes) == cudaSuccess &&
-         cudaFuncSetAttribute(k_sweep3<SWEEP_DOWNU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes) == cudaSuccess;
+  return prepare_mode<SWEEP_UP>() && prepare_mode<SWEEP_UPE>() && prepare_mode<SWEEP_DOWN>() &&
+         prepare_mode<SWEEP_DOWNU>();
 }
 
 template <int MODE>
 static void launch_mode(const Sweep3Params& p, const Sweep3Maps& maps, int ein, cudaStream_t s) {
+  using S = Shape<MODE>;
   dim3 grid;
   sweep3_grid(p.nc, p.zc, &grid);
-  k_sweep3<MODE><<<grid, NT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
+  k_sweep3<MODE, S::NT, S::MINB><<<grid, S::NT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
 }
 
 void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
