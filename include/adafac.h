@@ -228,6 +228,31 @@ adafac_status adafac_timing(adafac_handle h, int enable);
 adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
                                  int* launches);
 
+/* ||b - A u||_h (Eq. 10) for the uniform d-linear operator of
+ * -div(eps grad u) with scalar eps (Sec. 2.1) on a regular tree of depth
+ * `depth` in `dim` = 2 or 3 dimensions, computed WITHOUT ALLOCATING device
+ * memory.  The paper has no counterpart: this entry exists for callers that
+ * cannot allocate (a process whose device memory is fully committed, or one
+ * that must not pay the synchronisation of a device free).
+ *   u, b  device arrays of (3^depth + 1)^dim doubles, x fastest, boundary
+ *         ring included (its values are ignored); caller-owned, read only.
+ *   norm  device pointer to one double, written asynchronously on `stream`
+ *         (a cudaStream_t, NULL = legacy default stream).
+ * The per-block partial sums live in a fixed device array of the library
+ * (4096 doubles, one per 16384 vertices), so (3^depth + 1)^dim must be at most
+ * 4096 * 16384 = 67,108,864 vertices; larger trees return INVALID_ARG without
+ * launching.  Nothing in that array needs to start at zero: every partial the
+ * norm reads is written by the same call.
+ * The first call on each device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * outside any stream capture.  The array is shared by all calls on a device:
+ * calls that overlap in time (other streams, other host threads) race on it
+ * and may return wrong norms; order them on one stream.
+ * Returns INVALID_ARG (bad dim/depth/eps, null pointer, tree too large) or
+ * CUDA (launch failure); adafac_last_error is not updated by this call. */
+adafac_status adafac_residual_norm_static(int dim, int depth, double eps, const double* u,
+                                         const double* b, double* norm, void* stream);
+
 /* Message of the last failing call on h (or of the last failing setup when
  * h is NULL).  The pointer stays valid until the next call on h. */
 const char* adafac_last_error(adafac_handle h);

@@ -73,6 +73,7 @@ _SIGNATURES = [
     ("adafac_launch_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     ("adafac_timing", _I, [_P, _I]),
     ("adafac_timing_read", _I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    ("adafac_residual_norm_static", _I, [_I, _I, _D, _P, _P, _P, _P]),
     ("adafac_last_error", ctypes.c_char_p, [_P]),
     ("adafac_destroy", _I, [_P]),
 ]
@@ -120,6 +121,29 @@ def workspace_size(dim: int, depth: int, opts: Options) -> int:
     _check(lib.adafac_workspace_size(ctypes.byref(Tree(dim, depth)), ctypes.byref(opts),
                                      ctypes.byref(n)))
     return n.value
+
+
+def residual_norm_static(dim: int, depth: int, eps: float, u, b, norm, stream=None):
+    """||b - A u||_h (Eq. 10) of the uniform operator on device tensors u, b
+    ((3^depth+1)^dim float64 each), written into the 1-element float64 device
+    tensor ``norm`` on ``stream`` (default: torch's current stream).  The library
+    allocates nothing for this call (adafac_residual_norm_static)."""
+    import torch
+    lib = load()
+    for t in (u, b, norm):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous()):
+            raise TypeError("u, b and norm must be contiguous float64 CUDA tensors")
+    V = (3 ** depth + 1) ** dim
+    if u.numel() != V or b.numel() != V or norm.numel() < 1:
+        raise ValueError("u and b must hold (3^depth + 1)^dim values, norm at least one")
+    s = torch.cuda.current_stream() if stream is None else stream
+    st = lib.adafac_residual_norm_static(dim, depth, float(eps), ctypes.c_void_p(u.data_ptr()),
+                                         ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(norm.data_ptr()),
+                                         ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise AdafacError(st, "adafac_residual_norm_static failed")
 
 
 def _host_ptr(a: np.ndarray):
