@@ -92,6 +92,7 @@ struct adafac_handle_s {
   bool fast3 = false;
   float* e32b = nullptr;     // second correction buffer (ping-pong)
   int ebase = 0;             // which of e32 / e32b holds zeros at a step start
+  double* bq = nullptr;      // b / alpha (3-D uniform path)
   long long e_elems = 0;     // floats of e32 / e32b / rhs32 (padded rows on the 3-D path)
   int npartials = 0;
   int ldx = 0;               // row stride of the padded FP32 fine arrays
@@ -230,6 +231,7 @@ void carve(adafac_handle h, Carver& cv) {
   const long long Vf = h->lev[L].V;
   h->u = cv.take<double>(Vf);
   h->b = cv.take<double>(Vf);
+  if (h->fast3) h->bq = cv.take<double>(Vf);
   if (!h->eps_scalar) {
     h->eps = cv.take<double>(ipow_ll(h->lev[L].n, D));
     if (mixed) h->eps32 = cv.take<float>(ipow_ll(h->lev[L].n, D));
@@ -484,20 +486,22 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     rf.n = fine.n;
     rf.zc = kRefineZC;
     rf.ldx = h->ldx;
-    rf.a_c = a.cst[13];
-    rf.a_f = a.cst[12];
-    rf.a_e = a.cst[9];
-    rf.a_k = a.cst[0];
+    // A = alpha [32, 0, -2, -1]: the refinement residual sums the integer
+    // stencil exactly (checked to the last bits of the assembled coefficients)
+    rf.alpha = -a.cst[0];
+    const bool integer_stencil =
+        rf.alpha > 0.0 && std::fabs(a.cst[13] - 32.0 * rf.alpha) <= 1e-14 * a.cst[13] &&
+        std::fabs(a.cst[9] + 2.0 * rf.alpha) <= 1e-14 * rf.alpha;
     rf.hD = std::pow(1.0 / fine.n, 3);
     rf.u = h->u;
-    rf.b = h->b;
+    rf.bq = h->bq;
     rf.rhs32 = h->rhs32;
     rf.partials = h->partials;
     rf.ctl = h->ctl;
     h->ebase = 0;
     // the fused sweep evaluates the trilinear stencil without face terms,
     // which are exactly zero for the d-linear element in 3-D
-    if (a.cst[12] != 0.0 || !sweep3_prepare() ||
+    if (a.cst[12] != 0.0 || !integer_stencil || !sweep3_prepare() ||
         !sweep3_make_maps(h->e32, h->e32b, h->rhs32, fine.n, h->ldx, &h->maps)) {
       cudaGetLastError();
       h->fast3 = false;  // no tensor-map encoder: level-by-level kernels
@@ -508,6 +512,11 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
   c.tol = -1.0;
   c.set_r0 = 1;
   cudaMemcpyAsync(h->ctl, &c, sizeof(Control), cudaMemcpyHostToDevice, s);
+  if (h->fast3) {
+    // b / alpha and its largest exponent, for the fixed-point refinement residual
+    launch_scale(h->b, h->bq, fine.V, 1.0 / h->rf.alpha, s);
+    launch_max_exponent(h->bq, fine.V, &h->ctl->bexp, nullptr, s);
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda(h, "setup");
   return check_cuda(h, "setup");
 }
@@ -668,10 +677,13 @@ int fast3_step(adafac_handle h, int k, int ebase) {
   const int L = h->L;
   cudaStream_t s = h->stream;
   Refine3Params rf = h->rf;
+  // the scale of the fixed-point residual follows the largest |u|
+  cudaMemsetAsync(&h->ctl->uexp, 0, sizeof(int), s);
+  launch_max_exponent(h->u, h->lev[L].V, &h->ctl->uexp, h->ctl, s);
   timed(h, ADAFAC_KERNEL_REFINE, [&] { launch_refine3(rf, s); });
   launch_norm_finalize(h->partials, refine3_blocks(h->lev[L].n, kRefineZC), h->ctl, h->hist,
                        kHistCap, 0, s);
-  h->launches += 2;
+  h->launches += 3;
   Sweep3Params p = h->sw;
   p.q = L - 1 == 1 ? h->lev[1].g32 : h->lev[L - 1].t32;
   float* E[2] = {h->e32, h->e32b};

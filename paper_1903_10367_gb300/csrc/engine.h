@@ -60,6 +60,8 @@ struct Control {
   int set_r0;         // 1: the next norm evaluation defines r_0
   int fault;          // 1: a bounded device-side wait gave up (reported as TIMEOUT)
   int fault_info[8];  // where it gave up: mode, block, step index, slot, parity, z
+  int uexp;           // largest biased binary exponent of the fine iterate u
+  int bexp;           // largest biased binary exponent of b / alpha (3-D uniform path)
 };
 
 // ---- setup launches (FP64) -------------------------------------------------

@@ -43,13 +43,16 @@ constexpr int OW = 3 * BJX, OH = 3 * BJY;   // owned fine box (x, y): 60 x 24
 constexpr int NPAIR = 32;                   // thread column pairs
 constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane: 68 x 30
 constexpr int PLANE_F = 2048;               // floats per staged plane (128-byte multiple)
-constexpr int NSTAGE = 4, PREF = 3;         // ring slots, planes staged ahead
+constexpr int NSTAGE = 3, PREF = 2;         // ring slots, planes staged ahead
 constexpr int QW = BJX + 4, QH = BJY + 4;   // coarse q window, origin (J0x - 2, J0y - 2)
 constexpr int NQX = QH * 64;                // x-interpolated coarse values per plane
 constexpr int NJ = BJX * BJY;               // coarse columns of a block
 constexpr int CH = OH + 2;                  // up-pass rows (owned box + 1)
-constexpr int SR_P = 64;                    // pitch of the up-pass residual plane
-constexpr long kWaitLimit = 1L << 24;       // polls before a wait gives up
+// pitch of the up-pass residual plane: 3 SR_P = 2 (mod 32) spreads the
+// restriction windows of two coarse rows over distinct banks
+constexpr int SR_P = 86;
+constexpr long kWaitLimit = 1L << 22;       // polls before a wait gives up
+constexpr unsigned long long kWaitNs = 2000000000ull;  // or device time (2 s)
 static_assert(BOXW * BOXH <= PLANE_F, "staged box fits its slot");
 static_assert((BOXW * 4) % 16 == 0, "box rows are 16-byte multiples");
 static_assert(OW == 2 * (NPAIR - 2), "thread tiling of the owned box");
@@ -57,12 +60,15 @@ static_assert(OW == 2 * (NPAIR - 2), "thread tiling of the owned box");
 // t + PREF - NSTAGE <= t - 1, before the block barrier that opens step t
 static_assert(PREF < NSTAGE, "prefetch distance");
 
-// smem layout (floats): ring slots (e, rhs); then either the residual plane
-// sR (up-passes) or the coarse windows sQ[2], sQX[2] (down-passes); mbarriers
+// smem layout (floats): ring slots (e, rhs); then either the residual planes
+// sR[2] (up-passes) or the coarse windows sQ[3], sQX[2] (down-passes);
+// mbarriers.  The extra buffers let one block barrier per plane order all
+// hand-overs between threads.
 constexpr int OFF_SR = NSTAGE * 2 * PLANE_F;
+constexpr int SR_F = SR_P * CH;
 constexpr int OFF_Q = OFF_SR;
-constexpr int OFF_QX = OFF_Q + 2 * QW * QH;
-constexpr int END_SR = OFF_SR + SR_P * CH, END_Q = OFF_QX + 2 * NQX;
+constexpr int OFF_QX = OFF_Q + 3 * QW * QH + 2;  // (+2: 8-byte alignment)
+constexpr int END_SR = OFF_SR + 2 * SR_F, END_Q = OFF_QX + 2 * NQX;
 constexpr int OFF_BAR = END_SR > END_Q ? END_SR : END_Q;
 constexpr size_t SMEM_BYTES = (size_t)OFF_BAR * 4 + NSTAGE * 8 + 16;
 static_assert(OFF_SR % 2 == 0 && OFF_QX % 2 == 0 && OFF_BAR % 2 == 0, "8-byte alignment");
@@ -98,10 +104,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait on a phase of an mbarrier
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait on a phase of an mbarrier: gives up after kWaitNs of device
+// time or kWaitLimit polls, whichever comes first
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long i = 0; i < kWaitLimit; ++i)
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long i = 0; i < kWaitLimit; ++i) {
     if (mbar_try(bar, parity)) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 
@@ -260,7 +277,7 @@ __global__ void __launch_bounds__(NT, MINB)
   }
   float qa[NQ], qb[NQ];
   int qOz = -1;
-  auto make_q = [&](int s, int buf) {  // phase 1: sQ of plane s
+  auto make_q = [&](int s, int buf) {  // sQ of plane s, from cached coarse values
     const int Oz = min(max(s, 0) / 3, nc - 1);
     if (Oz != qOz) {
       const float* q0 = p.q + (long long)Oz * ncp1 * ncp1;
@@ -279,18 +296,22 @@ __global__ void __launch_bounds__(NT, MINB)
       if (e < QW * QH) sQ[buf * QW * QH + e] = fmaf(tz, qb[k] - qa[k], qa[k]);
     }
   };
-  auto make_qx = [&](int buf) {  // phase 2: sQX from sQ
-    const float* q = sQ + buf * QW * QH;
+  auto make_qx = [&](int qbuf, int buf) {  // sQX of a plane from its sQ
+    const float* q = sQ + qbuf * QW * QH;
 #pragma unroll
     for (int k = 0; k < NX; ++k) {
       const float v0 = q[xq[k]], v1 = q[xq[k] + 1];
       sQX[buf * NQX + tid + k * NT] = fmaf(xt[k], v1 - v0, v0);
     }
   };
+  // step t (down-pass plane s = t - 1) reads sQX[s & 1], forms sQX of plane
+  // s + 1 from sQ[mod3(s + 1)] and sQ of plane s + 2
+  auto mod3 = [](int v) { return ((v % 3) + 3) % 3; };
   if (DOWNP) {
-    make_q(t0 - 1, (t0 - 1) & 1);
+    make_q(t0 - 1, mod3(t0 - 1));
+    make_q(t0, mod3(t0));
     __syncthreads();
-    make_qx((t0 - 1) & 1);
+    make_qx(mod3(t0 - 1), (t0 - 1) & 1);
   }
   // ---- up-pass geometry: the pair (2 pc, 2 pc + 1) of sR is box columns
   // 1 + 2 pc (+1) (the owned box + 1 is box columns 2 .. 63); row strip RC + i
@@ -320,12 +341,14 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
   for (int i = 0; i < NPASS; ++i) accR[i][0] = accR[i][1] = accB[i][0] = accB[i][1] = 0.f;
 
-  for (int t = t0; t < t1; ++t) {
+  // UPE restricts plane t - 2 at step t: one step past the last load
+  const int tEnd = MODE == SWEEP_UPE ? t1 + 1 : t1;
+  for (int t = t0; t < tEnd; ++t) {
     __syncthreads();
     if (s_fail) break;
     if (tid == 0 && t + PREF < t1) issue(t + PREF);
     const int k = (t - t0) % NSTAGE;
-    if (!mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
+    if (t < t1 && !mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
       s_fail = t - t0 + 1;
       if (atomicCAS(p.fault, 0, 1) == 0) {  // the first failure records where
         p.fault_info[0] = MODE;
@@ -394,41 +417,57 @@ __global__ void __launch_bounds__(NT, MINB)
         }
       }
       if (t + 1 < t1) {
-        make_q(s + 1, (s + 1) & 1);
-        __syncthreads();
-        make_qx((s + 1) & 1);
+        make_qx(mod3(s + 1), (s + 1) & 1);
+        if (t + 2 < t1) make_q(s + 2, mod3(s + 2));
       }
       continue;
     }
-    // ---- up-pass: residual of plane r ---------------------------------------
-    const int r = MODE == SWEEP_UPE ? t - 1 : t;
+    // ---- up-pass: residual of plane t - 1 (UPE) ------------------------------
+    // UPE restricts the residual plane formed one step earlier; UP restricts
+    // the rhs plane staged in this step
+    const int r = MODE == SWEEP_UPE ? t - 2 : t;
     const bool doC = r >= zC0 && r < zC1;
     const float* wbase;
     int pitch;
     if (MODE == SWEEP_UPE) {
-      const float zm = (r >= 1 && r <= n - 1) ? 1.f : 0.f;
-      const float* E = sE + (rc0 + 1) * BOXW + 2 * pc;
-      const float* Rh = sRhs + (rc0 + 2) * BOXW + 1 + 2 * pc;
-      RowPair up = row_pair(E), ce = row_pair(E + BOXW);
+      const int rn = t - 1;
+      if (t < t1 && rn >= zC0 && rn < zC1) {
+        const float zm = (rn >= 1 && rn <= n - 1) ? 1.f : 0.f;
+        const float* E = sE + (rc0 + 1) * BOXW + 2 * pc;
+        const float* Rh = sRhs + (rc0 + 2) * BOXW + 1 + 2 * pc;
+        float* sRn = sR + (rn & 1) * SR_F;
+        RowPair up = row_pair(E), ce = row_pair(E + BOXW);
 #pragma unroll
-      for (int i = 0; i < RC; ++i) {
-        if (i >= ncrows) break;
-        const RowPair dn = row_pair(E + (i + 2) * BOXW);
-        const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
-        if (doC) {
+        for (int i = 0; i < RC; ++i) {
+          if (i >= ncrows) break;
+          const RowPair dn = row_pair(E + (i + 2) * BOXW);
+          const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
           const float2 Ae = add2(PR[i], q.Y);
           const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
           const float2 rho = mul2(fma2(Ae, neg1, rhs), mul2(mxC, f2(zm * myC[i])));
-          st2(sR + (rc0 + i) * SR_P + 2 * pc, rho);
+          st2(sRn + (rc0 + i) * SR_P + 2 * pc, rho);
+          PR[i] = add2(q.W, YR[i]);
+          YR[i] = q.Y;
+          up = ce;
+          ce = dn;
         }
-        PR[i] = add2(q.W, YR[i]);
-        YR[i] = q.Y;
-        up = ce;
-        ce = dn;
+      } else if (t < t1) {
+        // planes before the first residual plane: only roll the stencil parts
+        const float* E = sE + (rc0 + 1) * BOXW + 2 * pc;
+        RowPair up = row_pair(E), ce = row_pair(E + BOXW);
+#pragma unroll
+        for (int i = 0; i < RC; ++i) {
+          if (i >= ncrows) break;
+          const RowPair dn = row_pair(E + (i + 2) * BOXW);
+          const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+          PR[i] = add2(q.W, YR[i]);
+          YR[i] = q.Y;
+          up = ce;
+          ce = dn;
+        }
       }
-      __syncthreads();
       // sR column j is box column j + 1, row j box row j + 2
-      wbase = sR;
+      wbase = sR + (r & 1) * SR_F;
       pitch = SR_P;
     } else {
       // UP: rho = rhs (zero outside the interior), read from the staged box
@@ -524,19 +563,50 @@ __global__ void __launch_bounds__(NT, MINB)
   }
 }
 
-// FP64 residual of a uniform 3-D operator, z-marching with in-plane sums:
-// rhs32 = (float)(b - A u) and per-block sums of h^3 r^2.  With the face
-// coefficient zero (the d-linear element in 3-D), per plane p
-//   W_p = a_c u + a_e D_p,  Y_p = a_e X_p + a_k D_p,
-// X_p / D_p the sums of the 4 in-plane face / diagonal neighbours, and
-// (A u)_s = W_s + Y_{s-1} + Y_{s+1}: 14 FP64 operations per vertex, the
-// bound of this kernel on a GPU with few FP64 units.
+// Refinement residual of the uniform 3-D operator, z-marching with in-plane
+// sums: rhs32 = (float)(b - A u) and per-block sums of h^3 r^2.
+//
+// The d-linear stencil in 3-D is alpha [32, 0, -2, -1] (centre, faces, edges,
+// corners; alpha = eps h / 12), so A u = alpha S u with integer weights.  u and
+// b / alpha are converted to 64-bit fixed point with a common scale 2^F that
+// keeps every value below 2^56, and S u and b / alpha - S u are summed exactly
+// in integers: the only rounding is the conversion of each value (below
+// 2^-F, i.e. 2^-55 of the largest magnitude) and of the result to FP32.  This
+// is at least as accurate as FP64 arithmetic and runs on the integer units;
+// the GPU's FP64 rate (about 1/64 of FP32) would otherwise bound the kernel.
+// Per plane p, W_p = 32 u - 2 D_p and Y_p = -(2 X_p + D_p), with X_p / D_p the
+// sums of the 4 in-plane face / diagonal neighbours; (S u)_s = W_s + Y_{s-1} +
+// Y_{s+1}.
 constexpr int RT_X = 32, RT_Y = 8;
+
+// x * 2^F as an integer, F = 1078 - emax (emax >= the biased exponent of x);
+// values below 2^-1022 count as zero
+__device__ __forceinline__ long long to_fixed(double x, int emax) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const long long m = (long long)((bits & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = e - emax + 3;  // <= 3: |result| < 2^56
+  const long long v = sh >= 0 ? (m << sh) : (sh > -63 ? (m >> -sh) : 0);
+  return (bits >> 63) ? -v : v;
+}
+
+// |R| < 2^63 as a float, without cancellation
+__device__ __forceinline__ float fixed_to_float(long long R) {
+  const unsigned long long a = (unsigned long long)(R < 0 ? -R : R);
+  const float f = fmaf(__uint2float_rn((unsigned)(a >> 32)), 4294967296.f,
+                       __uint2float_rn((unsigned)(a & 0xffffffffu)));
+  return R < 0 ? -f : f;
+}
 
 __global__ void __launch_bounds__(RT_X* RT_Y) k_refine3(const Refine3Params p) {
   if (halted(p.ctl)) return;
-  __shared__ double sU[(RT_X + 2) * (RT_Y + 2)];
+  __shared__ long long sU[(RT_X + 2) * (RT_Y + 2)];
   __shared__ double red[RT_X * RT_Y / 32];
+  const int emax = max(max(p.ctl->uexp, p.ctl->bexp), 1);
+  const int F = 1078 - emax;
+  int ealpha;
+  const float malpha = (float)frexp(p.alpha, &ealpha);  // alpha = malpha 2^ealpha
   const int n = p.n, np1 = n + 1;
   const int tx = threadIdx.x % RT_X, ty = threadIdx.x / RT_X;
   const int x = blockIdx.x * RT_X + tx, y = blockIdx.y * RT_Y + ty;
@@ -544,46 +614,70 @@ __global__ void __launch_bounds__(RT_X* RT_Y) k_refine3(const Refine3Params p) {
   const int zhi = min(zlo + p.zc, n);            // planes [zlo, zhi)
   const bool inner = x >= 1 && x <= n - 1 && y >= 1 && y <= n - 1;
   constexpr int W = RT_X + 2;
-  const double ac = p.a_c, ae = p.a_e, ak = p.a_k;
-  double Wm = 0.0, Ym = 0.0, Ymm = 0.0;          // W_{z-1}, Y_{z-1}, Y_{z-2}
-  double acc = 0.0;
+  long long Wm = 0, Ym = 0, Ymm = 0;             // W_{z-1}, Y_{z-1}, Y_{z-2}
+  float acc = 0.f;                               // sum of (R 2^-32)^2
   for (int z = zlo - 1; z <= zhi; ++z) {
     for (int i = threadIdx.x; i < W * (RT_Y + 2); i += RT_X * RT_Y) {
       const int xx = blockIdx.x * RT_X - 1 + i % W, yy = blockIdx.y * RT_Y - 1 + i / W;
-      double v = 0.0;
+      long long v = 0;
       if (xx >= 0 && xx <= n && yy >= 0 && yy <= n && z >= 0 && z <= n)
-        v = p.u[((long long)z * np1 + yy) * np1 + xx];
+        v = to_fixed(p.u[((long long)z * np1 + yy) * np1 + xx], emax);
       sU[i] = v;
     }
     __syncthreads();
     const int ai = (ty + 1) * W + tx + 1;
-    const double X = (sU[ai - 1] + sU[ai + 1]) + (sU[ai - W] + sU[ai + W]);
-    const double D = (sU[ai - W - 1] + sU[ai - W + 1]) + (sU[ai + W - 1] + sU[ai + W + 1]);
-    const double Wz = fma(ae, D, ac * sU[ai]);
-    const double Yz = fma(ae, X, ak * D);
+    const long long X = (sU[ai - 1] + sU[ai + 1]) + (sU[ai - W] + sU[ai + W]);
+    const long long D = (sU[ai - W - 1] + sU[ai - W + 1]) + (sU[ai + W - 1] + sU[ai + W + 1]);
+    const long long Wz = sU[ai] * 32 - D * 2;
+    const long long Yz = -(X * 2 + D);
     __syncthreads();
     const int zz = z - 1;  // residual plane
     if (zz >= zlo && zz < zhi && inner) {
       const long long gi = ((long long)zz * np1 + y) * np1 + x;
-      const double r = ((p.b[gi] - Wm) - Ymm) - Yz;
-      p.rhs32[((long long)zz * np1 + y) * p.ldx + x] = (float)r;
-      acc = fma(r, r, acc);
+      const long long R = to_fixed(p.bq[gi], emax) - ((Wm + Ymm) + Yz);
+      const float Rf = fixed_to_float(R);
+      p.rhs32[((long long)zz * np1 + y) * p.ldx + x] = ldexpf(Rf * malpha, ealpha - F);
+      const float Rs = Rf * 2.3283064365386963e-10f;  // 2^-32
+      acc = fmaf(Rs, Rs, acc);
     }
     Ymm = Ym;
     Ym = Yz;
     Wm = Wz;
   }
   // block sum: warp shuffles, then the warps' partial sums
+  double dacc = (double)acc;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = acc;
+  for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = dacc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < RT_X * RT_Y / 32; ++w) t += red[w];
+    const double sc = ldexp(p.alpha, 32 - F);  // r = sc R 2^-32
     const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    p.partials[b] = t * p.hD;
+    p.partials[b] = t * sc * sc * p.hD;
   }
+}
+
+__global__ void k_max_exponent(const double* __restrict__ x, long long V, int* out,
+                               const Control* ctl) {
+  if (halted(ctl)) return;
+  unsigned m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned e =
+        (unsigned)(((unsigned long long)__double_as_longlong(x[i]) >> 52) & 0x7ff);
+    m = e > m ? e : m;
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, (int)m);
+}
+
+__global__ void k_scale(const double* __restrict__ b, double* __restrict__ bq, long long V,
+                        double inv_alpha) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
+       i += (long long)gridDim.x * blockDim.x)
+    bq[i] = b[i] * inv_alpha;
 }
 
 }  // namespace
@@ -679,6 +773,15 @@ int refine3_blocks(int n, int zc) {
   const int gx = (n + 1 + RT_X - 1) / RT_X, gy = (n + 1 + RT_Y - 1) / RT_Y;
   const int gz = (n - 1 + zc - 1) / zc;
   return gx * gy * gz;
+}
+
+void launch_max_exponent(const double* x, long long V, int* out, const Control* ctl,
+                         cudaStream_t s) {
+  k_max_exponent<<<152 * 8, 256, 0, s>>>(x, V, out, ctl);
+}
+
+void launch_scale(const double* b, double* bq, long long V, double inv_alpha, cudaStream_t s) {
+  k_scale<<<152 * 8, 256, 0, s>>>(b, bq, V, inv_alpha);
 }
 
 void launch_refine3(const Refine3Params& p, cudaStream_t s) {

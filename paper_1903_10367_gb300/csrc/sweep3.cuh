@@ -41,15 +41,18 @@ struct Sweep3Params {
   int* fault_info = nullptr;       // &ctl->fault_info[0]
 };
 
+// The refinement residual of the uniform 3-D operator A = alpha [32, 0, -2, -1]
+// (centre, faces, edges, corners): r = alpha (b / alpha - S u) with the integer
+// stencil S evaluated exactly in 64-bit fixed point.
 struct Refine3Params {
   int n = 0, zc = 0, ldx = 0;
-  double a_c = 0, a_f = 0, a_e = 0, a_k = 0;
+  double alpha = 0;                // eps h / 12
   double hD = 0;
   const double* u = nullptr;
-  const double* b = nullptr;
+  const double* bq = nullptr;      // b / alpha
   float* rhs32 = nullptr;          // padded FP32 layout (row stride ldx)
   double* partials = nullptr;
-  const Control* ctl = nullptr;
+  const Control* ctl = nullptr;    // uexp, bexp: exponents fixing the scale
 };
 
 // Tensor maps of the FP32 fine arrays for the staged loads.
@@ -68,5 +71,10 @@ void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int m
 void sweep3_grid(int nc, int zc, dim3* grid);
 int refine3_blocks(int n, int zc);
 void launch_refine3(const Refine3Params& p, cudaStream_t s);
+// *out = max(*out, largest biased exponent of x[0 .. V)); skipped once halted
+void launch_max_exponent(const double* x, long long V, int* out, const Control* ctl,
+                         cudaStream_t s);
+// bq = b * inv_alpha
+void launch_scale(const double* b, double* bq, long long V, double inv_alpha, cudaStream_t s);
 
 }  // namespace adafac

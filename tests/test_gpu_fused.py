@@ -102,3 +102,41 @@ def test_full_size_poisson3d_d5_mixed_fused():
     err4 = np.abs(S4.solution() - wl.manufactured_solution(3, 4)).max()
     S4.close()
     assert 8.0 < err4 / err5 < 10.0
+
+
+@pytest.mark.parametrize("scale", [2.0 ** 60, 2.0 ** -60])
+def test_fused_solve_is_exactly_scale_invariant(scale):
+    # the problem is linear: scaling f by a power of two scales every FP32 and
+    # FP64 value of the iteration by the same power, and the fixed-point
+    # refinement residual follows the magnitude of u -- the iterates must be
+    # the exactly scaled ones, with the same cycle count
+    f = wl.manufactured_rhs(3, 3)
+    o = adafac.default_options(precision="mixed", inner_cycles=5)
+    res = []
+    for s in (1.0, scale):
+        S = adafac.Solver(3, 3, 1.0, f * s, o)
+        c, rel = S.solve(1e-8, 500)
+        res.append((c, rel, S.solution()))
+        S.close()
+    assert res[0][0] == res[1][0]
+    assert res[0][1] == pytest.approx(res[1][1], rel=1e-12)
+    assert np.array_equal(res[0][2] * scale, res[1][2])
+
+
+def test_fused_refinement_residual_matches_the_oracle():
+    # the fixed-point refinement residual: its norm (recorded in the history
+    # when the next refinement step starts) equals the oracle's FP64 residual
+    # norm of the same iterate; the per-thread sums are FP32, hence 1e-6
+    L = 4
+    f = wl.manufactured_rhs(3, L)
+    S = adafac.Solver(3, L, 1.0, f, adafac.default_options(precision="mixed", inner_cycles=4))
+    S.cycle(4)
+    u4 = S.solution()
+    S.cycle(4)
+    h = S.history()
+    S.close()
+    H = oc.build_hierarchy(3, L, [1.0], True, f)
+    r0 = oc.residual_norm(H, H.b)
+    r4 = oc.residual_norm(H, oc.residual(H, L, u4, H.b))
+    assert h[0] == pytest.approx(1.0, rel=1e-6)
+    assert h[1] == pytest.approx(r4 / r0, rel=1e-6)
