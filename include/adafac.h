@@ -253,6 +253,70 @@ adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
 adafac_status adafac_residual_norm_static(int dim, int depth, double eps, const double* u,
                                          const double* b, double* norm, void* stream);
 
+/* ---- Request server: continuous batching of independent solves ---------
+ *
+ * Serving extension; the paper has no counterpart.  A server owns one device
+ * pool of device_bytes and n_streams CUDA streams on the device current at
+ * creation, and a host worker thread.  Submitted requests wait in a queue
+ * until their workspace (adafac_workspace_size) fits into the free part of
+ * the pool and fewer than max_running requests run; an admitted request is
+ * set up on one of the streams, then runs batches of cycles (inner_cycles for
+ * MIXED, 8 for FP64) until ||r||_h / ||r_0||_h <= rel_tol (Eq. 10) or
+ * max_cycles; requests on different streams overlap on the device, and
+ * requests submitted while others run are admitted as memory and slots free
+ * up.  At completion the solution is copied to host memory and the
+ * request's device memory returns to the pool.  Every function may be called
+ * from any host thread. */
+typedef struct adafac_server_s* adafac_server;
+
+enum {
+  ADAFAC_REQUEST_PENDING = 0,  /* queued, not yet admitted   */
+  ADAFAC_REQUEST_RUNNING = 1,  /* set up, cycles in progress */
+  ADAFAC_REQUEST_DONE = 2,     /* converged; solution ready  */
+  ADAFAC_REQUEST_FAILED = 3    /* ended with status != OK    */
+};
+
+typedef struct {
+  int state;          /* ADAFAC_REQUEST_*                                      */
+  int status;         /* final status code: OK when DONE, else the reason;
+                         NOT_CONVERGED still delivers the last iterate        */
+  int cycles;         /* cycles applied                                        */
+  double rel;         /* last evaluated ||r||_h / ||r_0||_h                    */
+  double queue_ms;    /* submission -> admission (-1 while queued)             */
+  double latency_ms;  /* submission -> solution in host memory (-1 until then) */
+} adafac_request_info;
+
+/* Allocates the pool (one cudaMalloc) and starts the worker.  OOM if the
+ * pool cannot be allocated; INVALID_ARG for n_streams outside 1..256 or
+ * max_running < 1. */
+adafac_status adafac_server_create(size_t device_bytes, int n_streams, int max_running,
+                                   adafac_server* out);
+
+/* Queues a solve; arguments as adafac_setup (host inputs, copied before the
+ * call returns) plus the tolerance and the cycle limit (>= 1).  *ticket
+ * identifies the request.  OOM when the request's workspace exceeds the
+ * whole pool (it could never run). */
+adafac_status adafac_submit(adafac_server s, const adafac_tree* tree, const double* eps,
+                            int eps_is_scalar, const double* f, const adafac_options* opt,
+                            double rel_tol, int max_cycles, int64_t* ticket);
+
+/* State, cycles, residual and timings of a request (non-blocking). */
+adafac_status adafac_poll(adafac_server s, int64_t ticket, adafac_request_info* info);
+
+/* For a request that has ended: copies its solution ((3^L+1)^dim doubles)
+ * into host memory dst (unless dst is NULL or the request produced none),
+ * forgets the ticket and returns the request's final status.  INVALID_ARG
+ * for unknown tickets and for requests still queued or running. */
+adafac_status adafac_fetch(adafac_server s, int64_t ticket, double* dst);
+
+/* Requests queued / running and pool bytes in use. */
+adafac_status adafac_server_stats(adafac_server s, int* pending, int* running,
+                                  size_t* bytes_in_use);
+
+/* Stops the worker (running requests end FAILED), frees the pool and
+ * forgets every ticket.  Synchronises. */
+adafac_status adafac_server_destroy(adafac_server s);
+
 /* Message of the last failing call on h (or of the last failing setup when
  * h is NULL).  The pointer stays valid until the next call on h. */
 const char* adafac_last_error(adafac_handle h);

@@ -42,6 +42,15 @@ class Tree(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("depth", ctypes.c_int)]
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("rel", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+REQUEST_STATE = {0: "pending", 1: "running", 2: "done", 3: "failed"}
+
+
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("transfer", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rtilde", ctypes.c_int),
@@ -74,6 +83,14 @@ _SIGNATURES = [
     ("adafac_timing", _I, [_P, _I]),
     ("adafac_timing_read", _I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     ("adafac_residual_norm_static", _I, [_I, _I, _D, _P, _P, _P, _P]),
+    ("adafac_server_create", _I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
+    ("adafac_submit", _I, [_P, ctypes.POINTER(Tree), _P, _I, _P, ctypes.POINTER(Options), _D,
+                           _I, ctypes.POINTER(ctypes.c_int64)]),
+    ("adafac_poll", _I, [_P, ctypes.c_int64, ctypes.POINTER(RequestInfo)]),
+    ("adafac_fetch", _I, [_P, ctypes.c_int64, _P]),
+    ("adafac_server_stats", _I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(ctypes.c_size_t)]),
+    ("adafac_server_destroy", _I, [_P]),
     ("adafac_last_error", ctypes.c_char_p, [_P]),
     ("adafac_destroy", _I, [_P]),
 ]
@@ -293,3 +310,67 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Server:
+    """Continuous-batching request server (adafac_server_*): solves submitted
+    from the host are admitted by device-memory footprint, run concurrently on
+    the server's streams and return their solutions to host memory."""
+
+    def __init__(self, device_bytes: int, n_streams: int = 16, max_running: int = 64):
+        self.lib = load()
+        self.s = ctypes.c_void_p()
+        st = self.lib.adafac_server_create(int(device_bytes), int(n_streams), int(max_running),
+                                           ctypes.byref(self.s))
+        if st != 0:
+            raise AdafacError(st, "adafac_server_create failed")
+
+    def submit(self, dim: int, depth: int, eps, f=None, opts: Options | None = None,
+               rel_tol: float = 1e-8, max_cycles: int = 2000) -> int:
+        opts = opts or default_options()
+        eps_is_scalar = np.isscalar(eps)
+        e = np.ascontiguousarray(np.atleast_1d(np.asarray(eps, dtype=np.float64)))
+        fa = None if f is None else np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+        t = ctypes.c_int64()
+        st = self.lib.adafac_submit(self.s, ctypes.byref(Tree(dim, depth)), _host_ptr(e),
+                                    int(eps_is_scalar), None if fa is None else _host_ptr(fa),
+                                    ctypes.byref(opts), float(rel_tol), int(max_cycles),
+                                    ctypes.byref(t))
+        if st != 0:
+            raise AdafacError(st, "adafac_submit failed")
+        self._shapes = getattr(self, "_shapes", {})
+        self._shapes[t.value] = (3 ** depth + 1,) * dim
+        return t.value
+
+    def poll(self, ticket: int) -> dict:
+        info = RequestInfo()
+        st = self.lib.adafac_poll(self.s, ctypes.c_int64(ticket), ctypes.byref(info))
+        if st != 0:
+            raise AdafacError(st, "adafac_poll: unknown ticket")
+        return {"state": REQUEST_STATE[info.state], "status": info.status, "cycles": info.cycles,
+                "rel": info.rel, "queue_ms": info.queue_ms, "latency_ms": info.latency_ms}
+
+    def fetch(self, ticket: int) -> np.ndarray:
+        out = np.empty(self._shapes[ticket])
+        st = self.lib.adafac_fetch(self.s, ctypes.c_int64(ticket), _host_ptr(out))
+        del self._shapes[ticket]
+        if st != 0:
+            raise AdafacError(st, f"request {ticket} ended with status {st}")
+        return out
+
+    def stats(self):
+        p, r, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(self.lib.adafac_server_stats(self.s, ctypes.byref(p), ctypes.byref(r),
+                                            ctypes.byref(b)))
+        return p.value, r.value, b.value
+
+    def close(self):
+        if self.s:
+            self.lib.adafac_server_destroy(self.s)
+            self.s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

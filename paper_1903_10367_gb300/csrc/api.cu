@@ -846,6 +846,21 @@ adafac_status reset_control(adafac_handle h) {
 
 }  // namespace
 
+namespace adafac {
+
+// Internal accessors for the request server (same library, not part of the
+// C ABI).
+Control* handle_control(adafac_handle h) { return h->ctl; }
+
+adafac_status handle_arm(adafac_handle h, double rel_tol) {
+  adafac_status st = write_ctl_field(h, offsetof(Control, tol), rel_tol);
+  if (st != ADAFAC_OK) return st;
+  int zero = 0;
+  return write_ctl_field(h, offsetof(Control, done), zero);
+}
+
+}  // namespace adafac
+
 extern "C" {
 
 adafac_status adafac_default_options(adafac_options* o) {

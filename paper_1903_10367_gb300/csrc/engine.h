@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "adafac.h"
+
 namespace adafac {
 
 constexpr int kMaxLevels = 16;
@@ -63,6 +65,11 @@ struct Control {
   int uexp;           // largest biased binary exponent of the fine iterate u
   int bexp;           // largest biased binary exponent of b / alpha (3-D uniform path)
 };
+
+// ---- handle internals used by the request server ---------------------------
+Control* handle_control(adafac_handle h);
+// ctl->tol = rel_tol, ctl->done = 0 (synchronises the handle's stream)
+adafac_status handle_arm(adafac_handle h, double rel_tol);
 
 // ---- setup launches (FP64) -------------------------------------------------
 template <int D>

@@ -89,3 +89,17 @@ def test_workspace_layout_is_consistent_for_every_option_combination(dim):
                         o = adafac.default_options(variant=variant, transfer=transfer,
                                                    precision=precision, rtilde=rtilde, form=form)
                         assert adafac.workspace_size(dim, 3, o) > 0
+
+
+def test_server_arguments_are_checked_before_any_device_call():
+    lib = adafac.load()
+    out = ctypes.c_void_p()
+    assert lib.adafac_server_create(1 << 20, 0, 4, ctypes.byref(out)) == 1
+    assert lib.adafac_server_create(1 << 20, 4, 0, ctypes.byref(out)) == 1
+    assert lib.adafac_server_create(16, 4, 4, ctypes.byref(out)) == 1
+    assert lib.adafac_server_create(1 << 20, 4, 4, None) == 1
+    assert not out.value
+    info = adafac.RequestInfo()
+    assert lib.adafac_poll(None, 1, ctypes.byref(info)) == 1
+    assert lib.adafac_fetch(None, 1, None) == 1
+    assert lib.adafac_server_destroy(None) == 1
