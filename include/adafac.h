@@ -256,11 +256,13 @@ adafac_status adafac_residual_norm_static(int dim, int depth, double eps, const 
 /* ---- Request server: continuous batching of independent solves ---------
  *
  * Serving extension; the paper has no counterpart.  A server owns one device
- * pool of device_bytes and n_streams CUDA streams on the device current at
- * creation, and a host worker thread.  Submitted requests wait in a queue
- * until their workspace (adafac_workspace_size) fits into the free part of
- * the pool and fewer than max_running requests run; an admitted request is
- * set up on one of the streams, then runs batches of cycles (inner_cycles for
+ * pool of device_bytes, n_streams CUDA streams on the device current at
+ * creation and host threads of its own.  Submitted requests wait in a queue until
+ * their workspace (adafac_workspace_size) fits into the free part of the pool
+ * and one of max_running slots is free; the request in slot i runs on stream
+ * i mod n_streams (n_streams >= max_running gives each its own stream);
+ * requests with workspaces up to 64 MiB use high-priority streams.  An
+ * admitted request is set up, then runs batches of cycles (inner_cycles for
  * MIXED, 8 for FP64) until ||r||_h / ||r_0||_h <= rel_tol (Eq. 10) or
  * max_cycles; requests on different streams overlap on the device, and
  * requests submitted while others run are admitted as memory and slots free
@@ -271,7 +273,7 @@ typedef struct adafac_server_s* adafac_server;
 
 enum {
   ADAFAC_REQUEST_PENDING = 0,  /* queued, not yet admitted   */
-  ADAFAC_REQUEST_RUNNING = 1,  /* set up, cycles in progress */
+  ADAFAC_REQUEST_RUNNING = 1,  /* admitted: in setup, cycles or completion */
   ADAFAC_REQUEST_DONE = 2,     /* converged; solution ready  */
   ADAFAC_REQUEST_FAILED = 3    /* ended with status != OK    */
 };
@@ -309,7 +311,7 @@ adafac_status adafac_poll(adafac_server s, int64_t ticket, adafac_request_info* 
  * for unknown tickets and for requests still queued or running. */
 adafac_status adafac_fetch(adafac_server s, int64_t ticket, double* dst);
 
-/* Requests queued / running and pool bytes in use. */
+/* Requests queued / admitted and not yet ended, and pool bytes in use. */
 adafac_status adafac_server_stats(adafac_server s, int* pending, int* running,
                                   size_t* bytes_in_use);
 

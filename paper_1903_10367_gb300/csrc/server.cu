@@ -1,23 +1,26 @@
 // Request server: continuous batching of independent adAFAC solves on one GPU.
 //
 // Requests (a tree, eps, f, options, tolerance) are submitted from any host
-// thread and queued with copies of their inputs.  A worker thread owns the
-// device:
-//   * admission -- a queued request is admitted when its workspace
-//     (adafac_workspace_size) fits into the free part of one device pool
-//     allocated when the server is created (first fit, 256-byte aligned,
-//     neighbouring free ranges merged).  A request that can never fit fails
-//     at once with ADAFAC_ERR_OOM;
-//   * setup -- an admitted request gets a handle on one of the server's
-//     streams (round robin) with its workspace carved from the pool;
-//   * cycles -- every running request without work in flight gets a batch of
-//     cycles (inner_cycles for MIXED, kBatchFP64 for FP64) and an asynchronous
-//     copy of its control block, both on its stream.  Requests on different
-//     streams overlap on the device; a request that arrives while others run
-//     joins at the next pass of the loop;
-//   * completion -- when a request's control block shows convergence,
-//     divergence or the cycle limit, its solution is copied to host memory,
-//     its handle destroyed and its workspace returned to the pool.
+// thread and queued with copies of their inputs.  Two host threads own the
+// device work:
+//   * service threads (kServiceThreads) admit a queued request when a running slot is free
+//     and its workspace (adafac_workspace_size) fits into the free part of one
+//     device pool allocated when the server is created (first fit, 256-byte
+//     aligned, neighbouring free ranges merged; the first 64 queued requests
+//     are scanned in submission order), and sets it up on the slot's stream
+//     with its workspace carved from the pool.  It also completes ended
+//     requests: their solution is copied to host memory, the handle destroyed
+//     and the workspace returned to the pool.  These calls wait on the device,
+//     so each service thread takes one such job at a time;
+//   * the launcher thread keeps one batch of cycles (inner_cycles for MIXED,
+//     kBatchFP64 for FP64) plus an asynchronous copy of the control block in
+//     flight for every running request, and never waits on the device.  When
+//     a copy shows convergence, divergence, a fault or the cycle limit, the
+//     request goes to the service threads.
+// Requests on different streams overlap on the device; small requests (up to
+// kSmallBytes of workspace) run on high-priority streams so that their short
+// kernels are scheduled ahead of the blocks of large ones.  A request submitted
+// while others run is admitted as soon as a slot and memory are free.
 // Latency is measured on the host from submission to the moment the solution
 // is in host memory.
 #include <algorithm>
@@ -40,6 +43,8 @@ using namespace adafac;
 namespace {
 
 constexpr int kBatchFP64 = 8;       // FP64 cycles enqueued per pass
+constexpr size_t kSmallBytes = 64u << 20;  // workspaces up to this run at high priority
+constexpr int kServiceThreads = 4;         // setups and completions in parallel
 constexpr size_t kAlign = 256;
 
 double now_ms() {
@@ -98,6 +103,7 @@ struct Request {
   std::vector<double> eps, f;
   double tol = 1e-8;
   int max_cycles = 0;
+  size_t need = 0;              // workspace bytes
   int state = ADAFAC_REQUEST_PENDING;
   adafac_status status = ADAFAC_OK;
   std::string error;
@@ -123,8 +129,8 @@ struct adafac_server_s {
   char* pool_base = nullptr;
   size_t pool_bytes = 0;
   Pool* pool = nullptr;
-  std::vector<cudaStream_t> streams;
-  int next_stream = 0;
+  std::vector<cudaStream_t> streams;       // lowest priority: large requests
+  std::vector<cudaStream_t> fast_streams;  // highest priority: small requests
   int max_running = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -133,7 +139,11 @@ struct adafac_server_s {
   std::map<int64_t, Request*> all;
   int64_t next_ticket = 1;
   std::atomic<bool> stop{false};
-  std::thread worker;
+  std::vector<Request*> completing;  // ended, waiting for a service thread
+  int in_setup = 0;                  // admitted, being set up
+  int in_completion = 0;             // ended, solution being copied
+  std::thread launcher;
+  std::vector<std::thread> service;
   int device = 0;
   Control* ctl_slots = nullptr;  // pinned, one per running request
   std::vector<int> free_slots;
@@ -155,7 +165,7 @@ void finish(adafac_server_s* S, Request* r, int state, adafac_status st, const s
   r->t_done = now_ms();
 }
 
-// releases the device resources of a running request (worker thread)
+// releases the device resources of a request
 void retire(adafac_server_s* S, Request* r) {
   if (r->h) adafac_destroy(r->h);
   r->h = nullptr;
@@ -169,24 +179,26 @@ void retire(adafac_server_s* S, Request* r) {
   r->bytes = 0;
 }
 
-bool admit_one(adafac_server_s* S, Request* r) {
-  size_t need = 0;
-  if (adafac_workspace_size(&r->tree, &r->opt, &need) != ADAFAC_OK) {
-    std::lock_guard<std::mutex> g(S->mu);
-    finish(S, r, ADAFAC_REQUEST_FAILED, ADAFAC_ERR_INVALID_ARG, "invalid tree or options");
-    return true;
-  }
-  {
-    std::lock_guard<std::mutex> g(S->mu);
-    if (S->free_slots.empty() || !S->pool->alloc(need, &r->off)) return false;
-    r->bytes = need;
-    r->slot = S->free_slots.back();
-    S->free_slots.pop_back();
-    r->host_ctl = S->ctl_slots + r->slot;
-  }
+// claims a slot and pool memory for a queued request (caller holds S->mu)
+bool claim(adafac_server_s* S, Request* r) {
+  if (S->free_slots.empty() || !S->pool->alloc(r->need, &r->off)) return false;
+  r->bytes = r->need;
+  r->slot = S->free_slots.back();
+  S->free_slots.pop_back();
+  r->host_ctl = S->ctl_slots + r->slot;
+  r->state = ADAFAC_REQUEST_RUNNING;  // admitted: memory and slot reserved
   r->t_admit = now_ms();
-  r->stream = S->streams[S->next_stream];
-  S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+  S->in_setup += 1;
+  return true;
+}
+
+// sets up a claimed request and hands it to the launcher (service thread)
+void admit(adafac_server_s* S, Request* r) {
+  // small solves go to high-priority streams, so that their short kernels
+  // are scheduled ahead of the blocks of large solves sharing the device
+  const bool small = r->bytes <= kSmallBytes;
+  const std::vector<cudaStream_t>& pool = small ? S->fast_streams : S->streams;
+  r->stream = pool[r->slot % (int)pool.size()];
   adafac_status st = adafac_setup(&r->tree, r->eps.data(), r->eps_scalar,
                                   r->f.empty() ? nullptr : r->f.data(), 0, &r->opt,
                                   S->pool_base + r->off, r->bytes, r->stream, &r->h);
@@ -198,14 +210,14 @@ bool admit_one(adafac_server_s* S, Request* r) {
     retire(S, r);
     std::lock_guard<std::mutex> g(S->mu);
     finish(S, r, ADAFAC_REQUEST_FAILED, st, why);
-    return true;
+    S->in_setup -= 1;
+    return;
   }
   r->inflight = false;
   r->enqueued = 0;
   std::lock_guard<std::mutex> g(S->mu);
-  r->state = ADAFAC_REQUEST_RUNNING;
   S->running.push_back(r->ticket);
-  return true;
+  S->in_setup -= 1;
 }
 
 // enqueue the next batch of a running request
@@ -221,11 +233,16 @@ void launch_batch(Request* r) {
   r->inflight = true;
 }
 
-// checks a request whose batch completed; true when it left the running set
-bool check_done(adafac_server_s* S, Request* r) {
+// true when the control block copied after the last batch ends the request
+bool ended(const Request* r) {
   const Control& c = *r->host_ctl;
-  const bool limit = r->enqueued >= r->max_cycles;
-  if (!(c.done || c.diverged || c.fault || limit)) return false;
+  return c.done || c.diverged || c.fault || r->enqueued >= r->max_cycles;
+}
+
+// copies the solution of an ended request to host memory and releases its
+// device resources (service thread)
+void complete(adafac_server_s* S, Request* r) {
+  const Control c = *r->host_ctl;
   std::vector<double> u;
   adafac_status st = ADAFAC_OK;
   std::string why;
@@ -246,38 +263,22 @@ bool check_done(adafac_server_s* S, Request* r) {
       why = adafac_last_error(r->h);
     }
   }
-  const int cycles = c.applied;
-  const double rel = c.rel;
   retire(S, r);
   std::lock_guard<std::mutex> g(S->mu);
   r->u.swap(u);
-  r->cycles = cycles;
-  r->rel = rel;
+  r->cycles = c.applied;
+  r->rel = c.rel;
   finish(S, r, st == ADAFAC_OK ? ADAFAC_REQUEST_DONE : ADAFAC_REQUEST_FAILED, st, why);
-  return true;
 }
 
-void worker_loop(adafac_server_s* S) {
+// Launcher: keeps a batch in flight for every running request and hands
+// ended requests to the service thread.  It never waits on the device.
+void launcher_loop(adafac_server_s* S) {
   cudaSetDevice(S->device);
+  std::vector<Request*> run;
   while (!S->stop.load()) {
     bool busy = false;
-    // admission, in submission order, of whatever fits
-    std::vector<Request*> cand;
-    {
-      std::lock_guard<std::mutex> g(S->mu);
-      const int room = S->max_running - (int)S->running.size();
-      for (size_t i = 0; i < S->pending.size() && (int)cand.size() < room && i < 64; ++i)
-        cand.push_back(S->all[S->pending[i]]);
-    }
-    for (Request* r : cand) {
-      if (admit_one(S, r)) {
-        busy = true;
-        std::lock_guard<std::mutex> g(S->mu);
-        S->pending.erase(std::find(S->pending.begin(), S->pending.end(), r->ticket));
-      }
-    }
-    // batches and completions
-    std::vector<Request*> run;
+    run.clear();
     {
       std::lock_guard<std::mutex> g(S->mu);
       for (int64_t t : S->running) run.push_back(S->all[t]);
@@ -292,36 +293,78 @@ void worker_loop(adafac_server_s* S) {
       if (q == cudaErrorNotReady) continue;
       busy = true;
       r->inflight = false;
-      bool left;
       if (q != cudaSuccess) {
         cudaGetLastError();
-        retire(S, r);
-        std::lock_guard<std::mutex> g(S->mu);
-        finish(S, r, ADAFAC_REQUEST_FAILED, ADAFAC_ERR_CUDA, cudaGetErrorString(q));
-        left = true;
-      } else {
-        left = check_done(S, r);
-        if (!left) launch_batch(r);
+        r->host_ctl->fault = 1;  // reported as a failed request
+      } else if (!ended(r)) {
+        launch_batch(r);
+        continue;
       }
-      if (left) {
-        std::lock_guard<std::mutex> g(S->mu);
-        S->running.erase(std::find(S->running.begin(), S->running.end(), r->ticket));
-        S->cv.notify_all();
-      }
+      std::lock_guard<std::mutex> g(S->mu);
+      S->running.erase(std::find(S->running.begin(), S->running.end(), r->ticket));
+      S->completing.push_back(r);
+      S->cv.notify_all();
     }
     if (!busy) {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait_for(lk, std::chrono::microseconds(50));
+      S->cv.wait_for(lk, std::chrono::microseconds(20));
     }
   }
-  // shutdown: let running work finish, then release it
-  std::vector<Request*> run;
+}
+
+// Service threads: completions (solution copies, releases) first, then
+// admissions (setups) -- the calls that wait on the device.  Each thread takes
+// one job at a time, so a long setup does not hold up other completions.
+void service_loop(adafac_server_s* S) {
+  cudaSetDevice(S->device);
+  while (!S->stop.load()) {
+    Request* job = nullptr;
+    bool completion = false;
+    {
+      std::lock_guard<std::mutex> g(S->mu);
+      if (!S->completing.empty()) {
+        job = S->completing.front();
+        S->completing.erase(S->completing.begin());
+        S->in_completion += 1;
+        completion = true;
+      } else {
+        // admission, in submission order, of the first request that fits
+        for (size_t i = 0; i < S->pending.size() && i < 64; ++i) {
+          Request* r = S->all[S->pending[i]];
+          if (claim(S, r)) {
+            S->pending.erase(S->pending.begin() + i);
+            job = r;
+            break;
+          }
+        }
+      }
+    }
+    if (job) {
+      if (completion) {
+        complete(S, job);
+        std::lock_guard<std::mutex> g(S->mu);
+        S->in_completion -= 1;
+      } else {
+        admit(S, job);
+      }
+      continue;
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv.wait_for(lk, std::chrono::microseconds(50));
+  }
+}
+
+// after both threads stopped: release whatever is still on the device
+void drain_all(adafac_server_s* S) {
+  std::vector<Request*> left;
   {
     std::lock_guard<std::mutex> g(S->mu);
-    for (int64_t t : S->running) run.push_back(S->all[t]);
+    for (int64_t t : S->running) left.push_back(S->all[t]);
     S->running.clear();
+    for (Request* r : S->completing) left.push_back(r);
+    S->completing.clear();
   }
-  for (Request* r : run) {
+  for (Request* r : left) {
     if (r->inflight) cudaEventSynchronize(r->ev);
     retire(S, r);
     std::lock_guard<std::mutex> g(S->mu);
@@ -363,13 +406,21 @@ adafac_status adafac_server_create(size_t device_bytes, int n_streams, int max_r
     return ADAFAC_ERR_OOM;
   }
   for (int i = max_running - 1; i >= 0; --i) S->free_slots.push_back(i);
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
   for (int i = 0; i < n_streams; ++i) {
-    cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, least) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, greatest) != cudaSuccess) {
       cudaGetLastError();
+      if (a) cudaStreamDestroy(a);
       break;
     }
-    S->streams.push_back(s);
+    S->streams.push_back(a);
+    S->fast_streams.push_back(b);
   }
   if (S->streams.empty()) {
     cudaFree(p);
@@ -377,7 +428,8 @@ adafac_status adafac_server_create(size_t device_bytes, int n_streams, int max_r
     delete S;
     return ADAFAC_ERR_CUDA;
   }
-  S->worker = std::thread(worker_loop, S);
+  S->launcher = std::thread(launcher_loop, S);
+  for (int i = 0; i < kServiceThreads; ++i) S->service.emplace_back(service_loop, S);
   *out = S;
   return ADAFAC_OK;
 }
@@ -405,6 +457,7 @@ adafac_status adafac_submit(adafac_server S, const adafac_tree* tree, const doub
   if (f) r->f.assign(f, f + vertices(*tree));
   r->tol = rel_tol;
   r->max_cycles = max_cycles;
+  r->need = need;
   r->t_submit = now_ms();
   std::lock_guard<std::mutex> g(S->mu);
   r->ticket = S->next_ticket++;
@@ -455,7 +508,9 @@ adafac_status adafac_server_stats(adafac_server S, int* pending, int* running,
   if (!S) return ADAFAC_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(S->mu);
   if (pending) *pending = (int)S->pending.size();
-  if (running) *running = (int)S->running.size();
+  if (running)
+    *running = (int)S->running.size() + S->in_setup + (int)S->completing.size() +
+               S->in_completion;
   if (bytes_in_use) *bytes_in_use = S->pool->used();
   return ADAFAC_OK;
 }
@@ -464,9 +519,13 @@ adafac_status adafac_server_destroy(adafac_server S) {
   if (!S) return ADAFAC_ERR_INVALID_ARG;
   S->stop.store(true);
   S->cv.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  if (S->launcher.joinable()) S->launcher.join();
+  for (std::thread& t : S->service)
+    if (t.joinable()) t.join();
+  drain_all(S);
   for (auto& kv : S->all) delete kv.second;
   for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+  for (cudaStream_t s : S->fast_streams) cudaStreamDestroy(s);
   cudaFreeHost(S->ctl_slots);
   cudaFree(S->pool_base);
   delete S->pool;

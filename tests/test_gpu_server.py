@@ -73,27 +73,29 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_admission_by_memory_runs_everything_within_the_budget():
-    cases = [c for c in _mix() if c[1] >= 4]
-    need = max(adafac.workspace_size(d, L, opts) for (d, L, _, _, opts) in cases)
+    # four solves of which only one fits into the pool at a time
+    opts = adafac.default_options(precision="mixed")
+    need = adafac.workspace_size(3, 4, opts)
     budget = int(need * 1.5)
     srv = adafac.Server(budget, n_streams=4, max_running=8)
-    tickets = [srv.submit(d, L, eps, f, opts) for (d, L, eps, f, opts) in cases]
+    f = wl.manufactured_rhs(3, 4)
+    tickets = [srv.submit(3, 4, 1.0, f * (k + 1), opts) for k in range(4)]
     peak = 0
     t0 = time.time()
     while time.time() - t0 < 120.0:
         p, r, b = srv.stats()
         peak = max(peak, b)
-        assert b <= budget
+        assert b <= budget and r <= 1
         if p == 0 and r == 0:
             break
-        time.sleep(0.001)
-    waited = 0
-    for t in tickets:
-        info = srv.poll(t)
+        time.sleep(0.0005)
+    infos = [srv.poll(t) for t in tickets]
+    for t, info in zip(tickets, infos):
         assert info["state"] == "done", info
-        waited += info["queue_ms"] > 0.5
         srv.fetch(t)
-    assert peak > 0 and waited >= 1  # some requests had to wait for memory
+    assert peak >= need
+    # each later request waited for the previous one to leave the pool
+    assert sum(i["queue_ms"] > 0.5 for i in infos) >= 3
     srv.close()
 
 

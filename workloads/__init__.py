@@ -166,3 +166,36 @@ WORKLOADS = {
 
 def get(name: str) -> Workload:
     return WORKLOADS[name]
+
+
+@dataclasses.dataclass(frozen=True)
+class ServingRequest:
+    """One solve of the serving stream: its tree, material and right-hand
+    side, and its arrival time on a unit-rate Poisson clock (multiply by the
+    mean inter-arrival time of the offered load)."""
+    index: int
+    dim: int
+    depth: int
+    eps: np.ndarray
+    f: np.ndarray
+    arrival: float
+
+
+def serving_requests(count: int, seed: int = 1903, low: float = 1e-2):
+    """The serving mix: 80 % 2-D solves with depth uniform in 3..6, 20 % 3-D
+    with depth uniform in 3..5; eps on blocks of level-min(3, depth-1) cells,
+    each block 1 or ``low`` with probability 1/2; f = 1; exponential
+    inter-arrival times of mean 1.  Request i draws from PCG64(seed) (shape and
+    arrival) and PCG64(seed + 1 + i) (its eps blocks)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        three_d = rng.uniform() < 0.2
+        dim = 3 if three_d else 2
+        depth = int(rng.integers(3, 6)) if three_d else int(rng.integers(3, 7))
+        t += float(rng.exponential(1.0))
+        block = 3 ** (depth - min(3, depth - 1))
+        eps = eps_random_blocks(dim, depth, block, low, seed + 1 + i)
+        out.append(ServingRequest(i, dim, depth, eps, constant_rhs(dim, depth), t))
+    return out
