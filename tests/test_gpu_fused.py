@@ -140,3 +140,36 @@ def test_fused_refinement_residual_matches_the_oracle():
     r4 = oc.residual_norm(H, oc.residual(H, L, u4, H.b))
     assert h[0] == pytest.approx(1.0, rel=1e-6)
     assert h[1] == pytest.approx(r4 / r0, rel=1e-6)
+
+
+def test_maximum_size_poisson3d_d6_mixed_fused():
+    # the largest tree of the suite: depth 6 (729^3 cells, 389 M vertices,
+    # about 34 GiB of workspace).  Sampled residuals use the oracle's assembled
+    # stencil (taken on a 3^3 grid and scaled by h, as the 3-D d-linear
+    # stiffness is proportional to h); their mean square estimates the
+    # normalised residual of Eq. 10, which must be at the tolerance.  The
+    # O(h^2) error against the depth-5 solve fixes the discretisation.
+    w6 = wl.get("poisson3d_d5").with_depth(6)
+    f6 = w6.f()
+    S = adafac.Solver(3, 6, 1.0, f6, adafac.default_options(precision="mixed"))
+    cycles, rel = S.solve(1e-8, 500)
+    u = S.solution()
+    S.close()
+    assert rel <= 1e-8
+    n = 729
+    st = fem.LevelOperator.from_eps(3, 3, [1.0], True).stencils()[1, 1, 1] * (3.0 / n)
+    rng = np.random.Generator(np.random.PCG64(7))
+    idx = rng.integers(1, n, size=(200000, 3))
+    b = (1.0 / n) ** 3 * f6[idx[:, 0], idx[:, 1], idx[:, 2]]
+    Au = np.zeros(len(idx))
+    for s, o in enumerate(fem.offsets(3)):
+        Au += st[s] * u[idx[:, 0] + o[0], idx[:, 1] + o[1], idx[:, 2] + o[2]]
+    est = np.sqrt(np.mean((b - Au) ** 2) / np.mean(b ** 2))
+    assert est <= 1.5e-8, est
+    err6 = np.abs(u - wl.manufactured_solution(3, 6)).max()
+    del u
+    S5 = adafac.Solver(3, 5, 1.0, w6.with_depth(5).f(), adafac.default_options(precision="mixed"))
+    S5.solve(1e-10, 500)
+    err5 = np.abs(S5.solution() - wl.manufactured_solution(3, 5)).max()
+    S5.close()
+    assert 8.0 < err5 / err6 < 10.0

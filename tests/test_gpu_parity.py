@@ -98,6 +98,8 @@ CASES = [
     (2, 4, "blocks", "boxmg", dict(variant="jac", form="fas")),
     (2, 4, "blocks", "boxmg", dict(variant="pi", form="fas")),
     (2, 1, "scalar", "dlinear", dict(variant="jac")),
+    (3, 1, "scalar", "dlinear", dict(variant="jac")),
+    (3, 1, "random", "boxmg", dict(variant="additive")),
     (2, 2, "random", "boxmg", dict(variant="jac")),
     (3, 3, "scalar", "dlinear", dict(variant="jac")),
     (3, 3, "random", "boxmg", dict(variant="jac")),
