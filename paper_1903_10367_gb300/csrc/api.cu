@@ -443,6 +443,9 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
       const int tiles = ((ncp1 + kSweepBJX - 1) / kSweepBJX) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);
       const int chunks = std::max(1, (3 * nsm) / tiles);
       sw.zc = std::max(3, (ncp1 + chunks - 1) / chunks);
+      const int tiles_d = ((3 * (ncp1 - 1) + 63) / 64) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);
+      const int chunks_d = std::max(1, (3 * nsm) / tiles_d);
+      sw.zc_down = std::max(3, (ncp1 + chunks_d - 1) / chunks_d);
     }
     sw.a_c = (float)a.cst[13];
     sw.a_f = (float)a.cst[12];

@@ -191,10 +191,15 @@ __global__ void __launch_bounds__(NT, MINB)
   const long long fplane = (long long)ldx * (n + 1);
   const int tid = threadIdx.x;
   const int pc = tid % NPAIR, strip = tid / NPAIR;
+  // up-passes own BJX x BJY coarse columns (their restriction targets); a
+  // down-pass owns 64 fine columns in x (all 32 pairs busy, no coarse
+  // alignment needed) and the same rows and planes
   const int Jx0 = blockIdx.x * BJX, Jy0 = blockIdx.y * BJY;
-  const int Jz0 = blockIdx.z * p.zc;
-  const int Jz1 = min(Jz0 + p.zc, ncp1);
-  const int xA = 3 * Jx0 - 4, yA = 3 * Jy0 - 4;            // staged box origin
+  const int zcm = DOWNP ? p.zc_down : p.zc;
+  const int Jz0 = blockIdx.z * zcm;
+  const int Jz1 = min(Jz0 + zcm, ncp1);
+  const int xA = DOWNP ? 64 * (int)blockIdx.x - 4 : 3 * Jx0 - 4;  // staged box origin
+  const int yA = 3 * Jy0 - 4;
   const int oz0 = 3 * Jz0 - 1, oz1 = 3 * Jz1 - 1;          // owned planes [oz0, oz1)
   const int zC0 = oz0 - 1, zC1 = oz1 + 1;                  // up-pass residual planes
   // step t stages e plane t and rhs plane t-1 (UP: rhs plane t).  Down-passes
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(NT, MINB)
 
   // ---- down-pass geometry: the pair (2 pc, 2 pc + 1) of the owned box is box
   // columns 3 + 2 pc (+1); row strip RB + i is box row 3 + strip RB + i
-  const int xb = xA + 3 + 2 * pc;                          // odd: 3 J0x - 1 + 2 pc
-  const bool pairB = DOWNP && pc < OW / 2;
+  const int xb = xA + 3 + 2 * pc;                          // odd
+  const bool pairB = DOWNP;
   const float2 mxB = make_float2(pairB && xb >= 1 && xb <= n - 1 ? 1.f : 0.f,
                                  pairB && xb + 1 >= 1 && xb + 1 <= n - 1 ? 1.f : 0.f);
   const int y0 = yA + 3 + strip * RB;
@@ -255,12 +260,15 @@ __global__ void __launch_bounds__(NT, MINB)
   // origin J0 - 2), then the x-interpolated values sQX at the owned columns;
   // each thread interpolates in y itself
   constexpr int NQ = (QW * QH + NT - 1) / NT, NX = NQX / NT;
+  // first coarse column of the window: the owned columns x in [xA + 3, xA + 67)
+  // interpolate between coarse columns floor(x / 3) and + 1
+  const int qx0 = max(xA + 3, 0) / 3 - 1;
   int qoff[NQ];
   bool qok[NQ];
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     const int e = tid + k * NT;
-    const int Jx = Jx0 - 2 + e % QW, Jy = Jy0 - 2 + e / QW;
+    const int Jx = qx0 + e % QW, Jy = Jy0 - 2 + e / QW;
     qok[k] = DOWNP && e < QW * QH && Jx >= 0 && Jx <= nc && Jy >= 0 && Jy <= nc;
     qoff[k] = qok[k] ? Jy * ncp1 + Jx : 0;
   }
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(NT, MINB)
     const int ky = e / 64, c = e % 64;
     const int x = xA + 3 + c;
     const int Ox = min(max(x, 0) / 3, nc - 1);
-    xq[k] = ky * QW + Ox - (Jx0 - 2);
+    xq[k] = ky * QW + Ox - qx0;
     xt[k] = (float)(x - 3 * Ox) * (1.f / 3.f);
   }
   float qa[NQ], qb[NQ];
@@ -718,6 +726,10 @@ void sweep3_grid(int nc, int zc, dim3* grid) {
   *grid = dim3((ncp1 + BJX - 1) / BJX, (ncp1 + BJY - 1) / BJY, (ncp1 + zc - 1) / zc);
 }
 
+void sweep3_grid_down(int nc, int zc, dim3* grid) {
+  const int ncp1 = nc + 1;
+  *grid = dim3((3 * nc + 63) / 64, (ncp1 + BJY - 1) / BJY, (ncp1 + zc - 1) / zc);
+}
 // threads and blocks per SM of each mode
 template <int MODE>
 struct Shape;
@@ -755,7 +767,10 @@ template <int MODE>
 static void launch_mode(const Sweep3Params& p, const Sweep3Maps& maps, int ein, cudaStream_t s) {
   using S = Shape<MODE>;
   dim3 grid;
-  sweep3_grid(p.nc, p.zc, &grid);
+  if (MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU)
+    sweep3_grid_down(p.nc, p.zc_down, &grid);
+  else
+    sweep3_grid(p.nc, p.zc, &grid);
   k_sweep3<MODE, S::NT, S::MINB><<<grid, S::NT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
 }
 

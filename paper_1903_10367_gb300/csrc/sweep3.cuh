@@ -12,13 +12,15 @@ namespace adafac {
 // DOWN: down-pass; DOWNU: last down-pass (u += e, the other buffer zeroed)
 enum SweepMode { SWEEP_UP = 0, SWEEP_UPE = 1, SWEEP_DOWN = 2, SWEEP_DOWNU = 3 };
 
-// coarse columns per block (x, y); the z extent is a launch parameter
+// coarse columns per block of the up-passes (x, y); the z extent is a launch
+// parameter
 constexpr int kSweepBJX = 20, kSweepBJY = 8;
 // staged box of a plane: x from 3 J0x - 4 (a 16-byte boundary), 68 x 30 floats
 constexpr int kBoxW = 3 * kSweepBJX + 8, kBoxH = 3 * kSweepBJY + 6;
 
 struct Sweep3Params {
   int n = 0, nc = 0, zc = 0;       // fine cells, coarse cells, coarse planes per block
+  int zc_down = 0;                 // coarse planes per block of the down-passes
   int ldx = 0;                     // row stride of the FP32 fine arrays (multiple of 4)
   // uniform stencil: A e = a_c e + a_f (6 faces) + a_e (12 edges) + a_k (8 corners)
   float a_c = 0, a_f = 0, a_e = 0, a_k = 0;
@@ -68,7 +70,8 @@ size_t sweep3_smem_bytes();
 bool sweep3_prepare();
 void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
                    cudaStream_t s);
-void sweep3_grid(int nc, int zc, dim3* grid);
+void sweep3_grid(int nc, int zc, dim3* grid);       // up-passes
+void sweep3_grid_down(int nc, int zc, dim3* grid);  // down-passes (64-column tiles)
 int refine3_blocks(int n, int zc);
 void launch_refine3(const Refine3Params& p, cudaStream_t s);
 // *out = max(*out, largest biased exponent of x[0 .. V)); skipped once halted
