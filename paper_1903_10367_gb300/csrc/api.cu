@@ -440,7 +440,7 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
       if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
       const int ncp1 = h->lev[L - 1].n + 1;
-      const int tiles = ((ncp1 + kSweepBJX - 1) / kSweepBJX) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);
+      const int tiles = ((ncp1 + kUpBJX - 1) / kUpBJX) * ((ncp1 + kUpBJY - 1) / kUpBJY);
       const int chunks = std::max(1, (3 * nsm) / tiles);
       sw.zc = std::max(3, (ncp1 + chunks - 1) / chunks);
       const int tiles_d = ((3 * (ncp1 - 1) + 63) / 64) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);

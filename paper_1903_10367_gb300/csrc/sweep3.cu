@@ -16,21 +16,24 @@
 // one: DOWN reads e and rhs and writes e (12 bytes per unknown), UPE reads e
 // and rhs (8 bytes per unknown).
 //
-// Blocking.  A block owns BJX x BJY coarse columns of level L-1 and zc coarse
-// planes, i.e. the fine vertices whose nearest coarse vertex lies in that box
-// (3 per coarse vertex and direction), and marches through its fine planes in
-// z.  A ring of NSTAGE shared-memory slots is filled by the tensor memory
-// accelerator PREF planes ahead of use: a slot holds a 68 x 30 box of e (the
-// owned box + 3 in x and y, its x origin on a 16-byte boundary) and of rhs;
-// one thread arms the slot's mbarrier with the byte count and issues the
-// copies; parts outside the domain are zero-filled.  A thread owns a pair of
-// adjacent columns and a strip of rows and works on the pair with packed
-// FP32x2 arithmetic.  The 27-point stencil is split into an in-plane part W_p
-// and an off-plane part Y_p per plane, A e(s) = W_s + Y_{s-1} + Y_{s+1}; the
-// partial sum W_s + Y_{s-1} and Y_s roll along in registers.  UPE forms rho on
-// the owned box + 1 (the support of the restriction) in shared memory and
-// accumulates the restriction and the damping right-hand side of the block's
-// coarse columns as the planes pass.
+// Both sweeps march through the planes of their block in z.  A ring of
+// NSTAGE shared-memory slots is filled by the tensor memory accelerator PREF
+// planes ahead of use: a slot holds a box of e and of rhs around the block's
+// columns (its x origin on a 16-byte boundary); one thread arms the slot's
+// mbarrier with the byte count and issues the copies; parts outside the domain
+// are zero-filled.  A thread owns a pair of adjacent columns and a strip of
+// rows and works on the pair with packed FP32x2 arithmetic.  The 27-point
+// stencil is split into an in-plane part W_p and an off-plane part Y_p per
+// plane, A e(s) = W_s + Y_{s-1} + Y_{s+1}; the partial sum W_s + Y_{s-1} and
+// Y_s roll along in registers.
+//   * Down-passes own 64 fine columns (the 32 lane pairs of a warp) and 24
+//     rows; they prolong q with the d-linear weights in three interpolation
+//     stages (z per plane, x per plane into shared memory, y per thread).
+//   * Up-passes own 41 x 4 coarse columns (their restriction targets; two
+//     x-tiles cover 82 coarse columns exactly), form rho on the owned box + 1
+//     (the support of the restriction) in shared memory, and accumulate the
+//     restriction and the damping right-hand side of their coarse columns as
+//     the planes pass.
 #include "common.cuh"
 #include "sweep3.cuh"
 
@@ -38,40 +41,35 @@ namespace adafac {
 
 namespace {
 
-constexpr int BJX = kSweepBJX, BJY = kSweepBJY;
-constexpr int OW = 3 * BJX, OH = 3 * BJY;   // owned fine box (x, y): 60 x 24
+// down-pass tiles: 64 fine columns x OH rows; the coarse window of the
+// prolongation is QW x QH coarse columns
+constexpr int BJY = kSweepBJY;
+constexpr int OH = 3 * BJY;                 // owned fine rows per block: 24
 constexpr int NPAIR = 32;                   // thread column pairs
 constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane: 68 x 30
 constexpr int PLANE_F = 2048;               // floats per staged plane (128-byte multiple)
 constexpr int NSTAGE = 3, PREF = 2;         // ring slots, planes staged ahead
-constexpr int QW = BJX + 4, QH = BJY + 4;   // coarse q window, origin (J0x - 2, J0y - 2)
+constexpr int QW = 24, QH = BJY + 4;        // coarse q window
 constexpr int NQX = QH * 64;                // x-interpolated coarse values per plane
-constexpr int NJ = BJX * BJY;               // coarse columns of a block
-constexpr int CH = OH + 2;                  // up-pass rows (owned box + 1)
-// pitch of the up-pass residual plane: 3 SR_P = 2 (mod 32) spreads the
-// restriction windows of two coarse rows over distinct banks
-constexpr int SR_P = 86;
+
 constexpr long kWaitLimit = 1L << 22;       // polls before a wait gives up
 constexpr unsigned long long kWaitNs = 2000000000ull;  // or device time (2 s)
 static_assert(BOXW * BOXH <= PLANE_F, "staged box fits its slot");
 static_assert((BOXW * 4) % 16 == 0, "box rows are 16-byte multiples");
-static_assert(OW == 2 * (NPAIR - 2), "thread tiling of the owned box");
+static_assert(BOXW >= 68 && BOXH >= OH + 6, "the box covers 64 columns and the rows + halo");
+
 // the slot refilled at step t (that of t + PREF) was last read at step
 // t + PREF - NSTAGE <= t - 1, before the block barrier that opens step t
 static_assert(PREF < NSTAGE, "prefetch distance");
 
-// smem layout (floats): ring slots (e, rhs); then either the residual planes
-// sR[2] (up-passes) or the coarse windows sQ[3], sQX[2] (down-passes);
-// mbarriers.  The extra buffers let one block barrier per plane order all
-// hand-overs between threads.
-constexpr int OFF_SR = NSTAGE * 2 * PLANE_F;
-constexpr int SR_F = SR_P * CH;
-constexpr int OFF_Q = OFF_SR;
+// down-pass smem layout (floats): ring slots (e, rhs), the coarse windows
+// sQ[3], sQX[2], mbarriers.  The extra buffers let one block barrier per plane
+// order all hand-overs between threads.
+constexpr int OFF_Q = NSTAGE * 2 * PLANE_F;
 constexpr int OFF_QX = OFF_Q + 3 * QW * QH + 2;  // (+2: 8-byte alignment)
-constexpr int END_SR = OFF_SR + 2 * SR_F, END_Q = OFF_QX + 2 * NQX;
-constexpr int OFF_BAR = END_SR > END_Q ? END_SR : END_Q;
+constexpr int OFF_BAR = OFF_QX + 2 * NQX;
 constexpr size_t SMEM_BYTES = (size_t)OFF_BAR * 4 + NSTAGE * 8 + 16;
-static_assert(OFF_SR % 2 == 0 && OFF_QX % 2 == 0 && OFF_BAR % 2 == 0, "8-byte alignment");
+static_assert(OFF_QX % 2 == 0 && OFF_BAR % 2 == 0, "8-byte alignment");
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -162,27 +160,24 @@ __device__ __forceinline__ Parts parts(const RowPair& up, const RowPair& ce, con
   return q;
 }
 
-// NT threads: 32 column pairs x NT/32 row strips; MINB blocks per SM
+// ---- down-passes ----------------------------------------------------------------
+// A block owns 64 fine columns in x (all 32 lane pairs busy; no coarse
+// alignment is needed), OH rows and zc_down coarse planes.  NT threads are 32
+// column pairs x NT/32 row strips; MINB blocks per SM.
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-    k_sweep3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
-             const __grid_constant__ CUtensorMap tm_rhs) {
-  constexpr bool DOWNP = MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU;
+    k_down3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
+            const __grid_constant__ CUtensorMap tm_rhs) {
+  static_assert(MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU, "down-pass modes");
   constexpr int NSTRIP = NT / NPAIR;
-  constexpr int RB = OH / NSTRIP;                        // down-pass rows per strip
-  constexpr int RCB = CH / NSTRIP, RCX = CH % NSTRIP;    // up-pass rows per strip:
-  constexpr int RC = RCB + (RCX ? 1 : 0);                // RCB + 1 for the first RCX
-  constexpr int NPASS = (NJ + NT - 1) / NT;              // restriction passes
+  constexpr int RB = OH / NSTRIP;                        // rows per strip
   static_assert(OH % NSTRIP == 0 && NQX % NT == 0, "thread tiling");
-  constexpr bool LOAD_E = MODE != SWEEP_UP;
   extern __shared__ __align__(128) float smem[];
   __shared__ int s_fail;
   if (halted(p.ctl)) return;
-  if (DOWNP && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
-      p.applied)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && p.applied)
     atomicAdd(p.applied, 1);  // one down-pass (a cycle's update) per launch
 
-  float* sR = smem + OFF_SR;
   float* sQ = smem + OFF_Q;
   float* sQX = smem + OFF_QX;
   const uint32_t bar0 = smem_addr(smem + OFF_BAR);
@@ -191,43 +186,22 @@ __global__ void __launch_bounds__(NT, MINB)
   const long long fplane = (long long)ldx * (n + 1);
   const int tid = threadIdx.x;
   const int pc = tid % NPAIR, strip = tid / NPAIR;
-  // up-passes own BJX x BJY coarse columns (their restriction targets); a
-  // down-pass owns 64 fine columns in x (all 32 pairs busy, no coarse
-  // alignment needed) and the same rows and planes
-  const int Jx0 = blockIdx.x * BJX, Jy0 = blockIdx.y * BJY;
-  const int zcm = DOWNP ? p.zc_down : p.zc;
-  const int Jz0 = blockIdx.z * zcm;
-  const int Jz1 = min(Jz0 + zcm, ncp1);
-  const int xA = DOWNP ? 64 * (int)blockIdx.x - 4 : 3 * Jx0 - 4;  // staged box origin
-  const int yA = 3 * Jy0 - 4;
+  const int Jy0 = blockIdx.y * BJY;
+  const int Jz0 = blockIdx.z * p.zc_down;
+  const int Jz1 = min(Jz0 + p.zc_down, ncp1);
+  const int xA = 64 * (int)blockIdx.x - 4, yA = 3 * Jy0 - 4;  // staged box origin
   const int oz0 = 3 * Jz0 - 1, oz1 = 3 * Jz1 - 1;          // owned planes [oz0, oz1)
-  const int zC0 = oz0 - 1, zC1 = oz1 + 1;                  // up-pass residual planes
-  // step t stages e plane t and rhs plane t-1 (UP: rhs plane t).  Down-passes
-  // update plane s = t-1 (W + Y of plane s-1.. s+1 known at step t), UPE forms
-  // the residual of plane t-1, UP restricts rhs plane t.
-  int t0, t1;
-  if (DOWNP) {
-    t0 = oz0 - 1;
-    t1 = oz1 + 1;
-  } else if (MODE == SWEEP_UPE) {
-    t0 = zC0 - 1;
-    t1 = zC1 + 1;
-  } else {
-    t0 = zC0;
-    t1 = zC1;
-  }
-  constexpr uint32_t kBytes = (LOAD_E ? 2 : 1) * BOXW * BOXH * 4;
+  // step t stages e plane t and rhs plane t-1 and updates plane s = t-1
+  // (W + Y of planes s-1 .. s+1 are known at step t)
+  const int t0 = oz0 - 1, t1 = oz1 + 1;
+  constexpr uint32_t kBytes = 2 * BOXW * BOXH * 4;
   auto issue = [&](int t) {
     const int k = (t - t0) % NSTAGE;
     const uint32_t bar = bar0 + 8 * k;
     float* slot = smem + k * 2 * PLANE_F;
     mbar_expect(bar, kBytes);
-    if (LOAD_E) {
-      tma_load(smem_addr(slot), &tm_e, xA, yA, t, bar);
-      tma_load(smem_addr(slot + PLANE_F), &tm_rhs, xA, yA, t - 1, bar);
-    } else {
-      tma_load(smem_addr(slot + PLANE_F), &tm_rhs, xA, yA, t, bar);
-    }
+    tma_load(smem_addr(slot), &tm_e, xA, yA, t, bar);
+    tma_load(smem_addr(slot + PLANE_F), &tm_rhs, xA, yA, t - 1, bar);
   };
   if (tid == 0) {
     s_fail = 0;
@@ -238,12 +212,11 @@ __global__ void __launch_bounds__(NT, MINB)
   if (tid == 0)
     for (int t = t0; t < t0 + PREF && t < t1; ++t) issue(t);
 
-  // ---- down-pass geometry: the pair (2 pc, 2 pc + 1) of the owned box is box
-  // columns 3 + 2 pc (+1); row strip RB + i is box row 3 + strip RB + i
+  // the pair (2 pc, 2 pc + 1) of the owned box is box columns 3 + 2 pc (+1);
+  // row strip RB + i is box row 3 + strip RB + i
   const int xb = xA + 3 + 2 * pc;                          // odd
-  const bool pairB = DOWNP;
-  const float2 mxB = make_float2(pairB && xb >= 1 && xb <= n - 1 ? 1.f : 0.f,
-                                 pairB && xb + 1 >= 1 && xb + 1 <= n - 1 ? 1.f : 0.f);
+  const float2 mxB = make_float2(xb >= 1 && xb <= n - 1 ? 1.f : 0.f,
+                                 xb + 1 >= 1 && xb + 1 <= n - 1 ? 1.f : 0.f);
   const int y0 = yA + 3 + strip * RB;
   float myB[RB];
   int qrB[RB];
@@ -257,11 +230,10 @@ __global__ void __launch_bounds__(NT, MINB)
     tyB[i] = (float)(y - 3 * Oy) * (1.f / 3.f);
   }
   // prolongation of q: per plane the z-interpolated coarse window sQ (QW x QH,
-  // origin J0 - 2), then the x-interpolated values sQX at the owned columns;
-  // each thread interpolates in y itself
+  // origin (qx0, J0y - 2)), then the x-interpolated values sQX at the owned
+  // columns; each thread interpolates in y itself.  The owned columns x in
+  // [xA + 3, xA + 67) interpolate between coarse columns floor(x / 3) and + 1.
   constexpr int NQ = (QW * QH + NT - 1) / NT, NX = NQX / NT;
-  // first coarse column of the window: the owned columns x in [xA + 3, xA + 67)
-  // interpolate between coarse columns floor(x / 3) and + 1
   const int qx0 = max(xA + 3, 0) / 3 - 1;
   int qoff[NQ];
   bool qok[NQ];
@@ -269,7 +241,7 @@ __global__ void __launch_bounds__(NT, MINB)
   for (int k = 0; k < NQ; ++k) {
     const int e = tid + k * NT;
     const int Jx = qx0 + e % QW, Jy = Jy0 - 2 + e / QW;
-    qok[k] = DOWNP && e < QW * QH && Jx >= 0 && Jx <= nc && Jy >= 0 && Jy <= nc;
+    qok[k] = e < QW * QH && Jx >= 0 && Jx <= nc && Jy >= 0 && Jy <= nc;
     qoff[k] = qok[k] ? Jy * ncp1 + Jx : 0;
   }
   int xq[NX];
@@ -312,51 +284,29 @@ __global__ void __launch_bounds__(NT, MINB)
       sQX[buf * NQX + tid + k * NT] = fmaf(xt[k], v1 - v0, v0);
     }
   };
-  // step t (down-pass plane s = t - 1) reads sQX[s & 1], forms sQX of plane
-  // s + 1 from sQ[mod3(s + 1)] and sQ of plane s + 2
+  // step t (plane s = t - 1) reads sQX[s & 1], forms sQX of plane s + 1 from
+  // sQ[mod3(s + 1)] and sQ of plane s + 2: one block barrier per plane orders
+  // every hand-over
   auto mod3 = [](int v) { return ((v % 3) + 3) % 3; };
-  if (DOWNP) {
-    make_q(t0 - 1, mod3(t0 - 1));
-    make_q(t0, mod3(t0));
-    __syncthreads();
-    make_qx(mod3(t0 - 1), (t0 - 1) & 1);
-  }
-  // ---- up-pass geometry: the pair (2 pc, 2 pc + 1) of sR is box columns
-  // 1 + 2 pc (+1) (the owned box + 1 is box columns 2 .. 63); row strip RC + i
-  // is box row 2 + strip RC + i
-  const int xc = xA + 1 + 2 * pc;
-  const float2 mxC = make_float2(xc >= 1 && xc <= n - 1 ? 1.f : 0.f,
-                                 xc + 1 >= 1 && xc + 1 <= n - 1 ? 1.f : 0.f);
-  const int rc0 = strip * RCB + min(strip, RCX);           // first up-pass row
-  const int ncrows = RCB + (strip < RCX ? 1 : 0);
-  float myC[RC];
-#pragma unroll
-  for (int i = 0; i < RC; ++i) {
-    const int y = yA + 2 + rc0 + i;
-    myC[i] = (i < ncrows && y >= 1 && y <= n - 1) ? 1.f : 0.f;
-  }
+  make_q(t0 - 1, mod3(t0 - 1));
+  make_q(t0, mod3(t0));
+  __syncthreads();
+  make_qx(mod3(t0 - 1), (t0 - 1) & 1);
 
   const float2 ac2 = f2(p.a_c), ae2 = f2(p.a_e), ak2 = f2(p.a_k), w2 = f2(p.w_invd);
   const float2 neg1 = f2(-1.f);
   // rolling stencil parts per row: centre of the last plane, PR = W_s + Y_{s-1}
   // of the last plane s, YR = Y_s
-  float2 eR[RC], PR[RC], YR[RC];
+  float2 eR[RB], PR[RB], YR[RB];
 #pragma unroll
-  for (int i = 0; i < RC; ++i) eR[i] = PR[i] = YR[i] = f2(0.f);
-  // restriction accumulators: coarse columns tid, tid + NT, ..., two coarse
-  // planes in flight (by parity)
-  float accR[NPASS][2], accB[NPASS][2];
-#pragma unroll
-  for (int i = 0; i < NPASS; ++i) accR[i][0] = accR[i][1] = accB[i][0] = accB[i][1] = 0.f;
+  for (int i = 0; i < RB; ++i) eR[i] = PR[i] = YR[i] = f2(0.f);
 
-  // UPE restricts plane t - 2 at step t: one step past the last load
-  const int tEnd = MODE == SWEEP_UPE ? t1 + 1 : t1;
-  for (int t = t0; t < tEnd; ++t) {
+  for (int t = t0; t < t1; ++t) {
     __syncthreads();
     if (s_fail) break;
     if (tid == 0 && t + PREF < t1) issue(t + PREF);
     const int k = (t - t0) % NSTAGE;
-    if (t < t1 && !mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
+    if (!mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
       s_fail = t - t0 + 1;
       if (atomicCAS(p.fault, 0, 1) == 0) {  // the first failure records where
         p.fault_info[0] = MODE;
@@ -371,186 +321,285 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     const float* sE = smem + k * 2 * PLANE_F;
     const float* sRhs = sE + PLANE_F;
-    if (DOWNP) {
-      // ---- down-pass: new e at plane s = t - 1 on the owned box ----------
-      const int s = t - 1;
-      if (pairB) {
-        const bool doB = s >= oz0 && s < oz1 && s >= 1 && s <= n - 1;
-        const float* E = sE + (strip * RB + 2) * BOXW + 2 + 2 * pc;
-        const float* Rh = sRhs + (strip * RB + 3) * BOXW + 3 + 2 * pc;
-        const float* qx = sQX + (s & 1) * NQX;
-        // DOWNU: fetch the FP64 iterate first (its latency overlaps the stencil)
-        double uo[RB][2];
-        if (MODE == SWEEP_DOWNU && doB) {
+    const int s = t - 1;
+    const bool doB = s >= oz0 && s < oz1 && s >= 1 && s <= n - 1;
+    const float* E = sE + (strip * RB + 2) * BOXW + 2 + 2 * pc;
+    const float* Rh = sRhs + (strip * RB + 3) * BOXW + 3 + 2 * pc;
+    const float* qx = sQX + (s & 1) * NQX;
+    // DOWNU: fetch the FP64 iterate first (its latency overlaps the stencil)
+    double uo[RB][2];
+    if (MODE == SWEEP_DOWNU && doB) {
 #pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
-            uo[i][0] = (myB[i] != 0.f && mxB.x != 0.f) ? p.u[urow + xb] : 0.0;
-            uo[i][1] = (myB[i] != 0.f && mxB.y != 0.f) ? p.u[urow + xb + 1] : 0.0;
-          }
-        }
-        RowPair up = row_pair(E), ce = row_pair(E + BOXW);
-#pragma unroll
-        for (int i = 0; i < RB; ++i) {
-          const RowPair dn = row_pair(E + (i + 2) * BOXW);
-          const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
-          if (doB && myB[i] != 0.f) {
-            const float2 Ae = add2(PR[i], q.Y);
-            const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
-            const float2 rho = fma2(Ae, neg1, rhs);
-            const float2 q0 = ld2(qx + qrB[i]), q1 = ld2(qx + qrB[i] + 64);
-            const float2 pq = fma2(f2(tyB[i]), fma2(q0, neg1, q1), q0);
-            const float2 ek = add2(fma2(w2, rho, eR[i]), pq);
-            float* eo = p.e_out + s * fplane + (long long)(y0 + i) * ldx + xb;
-            if (MODE == SWEEP_DOWN) {
-              if (mxB.x != 0.f) eo[0] = ek.x;
-              if (mxB.y != 0.f) eo[1] = ek.y;
-            } else {
-              const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
-              if (mxB.x != 0.f) {
-                p.u[urow + xb] = uo[i][0] + (double)ek.x;
-                eo[0] = 0.f;
-              }
-              if (mxB.y != 0.f) {
-                p.u[urow + xb + 1] = uo[i][1] + (double)ek.y;
-                eo[1] = 0.f;
-              }
-            }
-          }
-          PR[i] = add2(q.W, YR[i]);
-          YR[i] = q.Y;
-          eR[i] = ce.c;
-          up = ce;
-          ce = dn;
-        }
+      for (int i = 0; i < RB; ++i) {
+        const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
+        uo[i][0] = (myB[i] != 0.f && mxB.x != 0.f) ? p.u[urow + xb] : 0.0;
+        uo[i][1] = (myB[i] != 0.f && mxB.y != 0.f) ? p.u[urow + xb + 1] : 0.0;
       }
-      if (t + 1 < t1) {
-        make_qx(mod3(s + 1), (s + 1) & 1);
-        if (t + 2 < t1) make_q(s + 2, mod3(s + 2));
-      }
-      continue;
     }
-    // ---- up-pass: residual of plane t - 1 (UPE) ------------------------------
-    // UPE restricts the residual plane formed one step earlier; UP restricts
-    // the rhs plane staged in this step
-    const int r = MODE == SWEEP_UPE ? t - 2 : t;
-    const bool doC = r >= zC0 && r < zC1;
+    RowPair up = row_pair(E), ce = row_pair(E + BOXW);
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      const RowPair dn = row_pair(E + (i + 2) * BOXW);
+      const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+      if (doB && myB[i] != 0.f) {
+        const float2 Ae = add2(PR[i], q.Y);
+        const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
+        const float2 rho = fma2(Ae, neg1, rhs);
+        const float2 q0 = ld2(qx + qrB[i]), q1 = ld2(qx + qrB[i] + 64);
+        const float2 pq = fma2(f2(tyB[i]), fma2(q0, neg1, q1), q0);
+        const float2 ek = add2(fma2(w2, rho, eR[i]), pq);
+        float* eo = p.e_out + s * fplane + (long long)(y0 + i) * ldx + xb;
+        if (MODE == SWEEP_DOWN) {
+          if (mxB.x != 0.f) eo[0] = ek.x;
+          if (mxB.y != 0.f) eo[1] = ek.y;
+        } else {
+          const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
+          if (mxB.x != 0.f) {
+            p.u[urow + xb] = uo[i][0] + (double)ek.x;
+            eo[0] = 0.f;  // the zero buffer of the next refinement step
+          }
+          if (mxB.y != 0.f) {
+            p.u[urow + xb + 1] = uo[i][1] + (double)ek.y;
+            eo[1] = 0.f;
+          }
+        }
+      }
+      PR[i] = add2(q.W, YR[i]);
+      YR[i] = q.Y;
+      eR[i] = ce.c;
+      up = ce;
+      ce = dn;
+    }
+    if (t + 1 < t1) {
+      make_qx(mod3(s + 1), (s + 1) & 1);
+      if (t + 2 < t1) make_q(s + 2, mod3(s + 2));
+    }
+  }
+  __syncthreads();
+  if (s_fail && tid == 0) {
+    atomicExch(p.fault, 1);
+    // let the copies still in flight (steps tf .. tf + PREF) land before the
+    // block's shared memory is released
+    const int tf = t0 + s_fail - 1;
+    for (int tt = tf; tt <= tf + PREF && tt < t1; ++tt) {
+      const uint32_t bar = bar0 + 8 * ((tt - t0) % NSTAGE);
+      const uint32_t par = ((tt - t0) / NSTAGE) & 1;
+      for (long i = 0; i < kWaitLimit / 16 && !mbar_try(bar, par); ++i) {
+      }
+    }
+  }
+}
+
+// ---- up-passes on wide tiles -------------------------------------------------
+// A block owns UBJX x UBJY coarse columns (41 x 4: two x-tiles cover the 82
+// coarse columns of a 243-cell grid exactly) and zc coarse planes.  Its 256
+// threads are 64 column pairs (two warps per row) x 4 row strips.  The
+// residual region is the owned fine box + 1 (125 x 14 fine columns), computed
+// by 63 pairs whose first column is odd, starting at cstart = 3 J0x - 2 (J0x
+// odd) or 3 J0x - 3 (J0x even); the staged box starts at the 16-byte boundary
+// at or below cstart - 1 and is 132 x 16 floats.
+constexpr int UBJX = kUpBJX, UBJY = kUpBJY;
+constexpr int UNT = 256, UNPAIR = 64, UNSTRIP = UNT / UNPAIR;
+constexpr int UBOXW = kUpBoxW, UBOXH = kUpBoxH;
+constexpr int UPLANE_F = UBOXW * UBOXH;                 // 2112 floats: 128-byte multiple
+constexpr int UCH = 3 * UBJY + 2;                       // residual rows (14)
+constexpr int URCB = UCH / UNSTRIP, URCX = UCH % UNSTRIP;
+constexpr int URC = URCB + (URCX ? 1 : 0);
+constexpr int USR_P = 130;                              // residual-plane pitch
+constexpr int USR_F = USR_P * UCH;
+constexpr int UNJ = UBJX * UBJY;                        // 164 coarse columns
+constexpr int UOFF_SR = NSTAGE * 2 * UPLANE_F;
+constexpr int UOFF_BAR = UOFF_SR + 2 * USR_F;
+constexpr size_t USMEM_BYTES = (size_t)UOFF_BAR * 4 + NSTAGE * 8 + 16;
+static_assert((UPLANE_F * 4) % 128 == 0 && UOFF_SR % 2 == 0 && UOFF_BAR % 2 == 0, "alignment");
+static_assert(UNJ <= UNT && 2 * (UNPAIR - 1) >= 3 * UBJX + 3, "thread counts");
+
+template <int MODE>
+__global__ void __launch_bounds__(UNT, 3)
+    k_up3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
+          const __grid_constant__ CUtensorMap tm_rhs) {
+  static_assert(MODE == SWEEP_UP || MODE == SWEEP_UPE, "up-pass modes");
+  extern __shared__ __align__(128) float smem[];
+  __shared__ int s_fail;
+  if (halted(p.ctl)) return;
+  float* sR = smem + UOFF_SR;
+  const uint32_t bar0 = smem_addr(smem + UOFF_BAR);
+  const int n = p.n, nc = p.nc, ncp1 = nc + 1;
+  const int tid = threadIdx.x;
+  const int pc = tid % UNPAIR, strip = tid / UNPAIR;
+  const int Jx0 = blockIdx.x * UBJX, Jy0 = blockIdx.y * UBJY;
+  const int Jz0 = blockIdx.z * p.zc;
+  const int Jz1 = min(Jz0 + p.zc, ncp1);
+  const int soff = (Jx0 & 1) ? 0 : 1;                   // restriction column offset in sR
+  const int cstart = 3 * Jx0 - 2 - soff;                // odd
+  const int xA = ((cstart - 1) >> 2) << 2;              // floor to a multiple of 4
+  const int yA = 3 * Jy0 - 3;                           // box row i + 1 = residual row i
+  const int oz0 = 3 * Jz0 - 1, oz1 = 3 * Jz1 - 1;
+  const int zC0 = oz0 - 1, zC1 = oz1 + 1;
+  constexpr bool UPE = MODE == SWEEP_UPE;
+  const int t0 = UPE ? zC0 - 1 : zC0, t1 = UPE ? zC1 + 1 : zC1;
+  constexpr uint32_t kBytes = (UPE ? 2 : 1) * UBOXW * UBOXH * 4;
+  auto issue = [&](int t) {
+    const int k = (t - t0) % NSTAGE;
+    const uint32_t bar = bar0 + 8 * k;
+    float* slot = smem + k * 2 * UPLANE_F;
+    mbar_expect(bar, kBytes);
+    if (UPE) {
+      tma_load(smem_addr(slot), &tm_e, xA, yA, t, bar);
+      tma_load(smem_addr(slot + UPLANE_F), &tm_rhs, xA, yA, t - 1, bar);
+    } else {
+      tma_load(smem_addr(slot + UPLANE_F), &tm_rhs, xA, yA, t, bar);
+    }
+  };
+  if (tid == 0) {
+    s_fail = 0;
+    for (int k = 0; k < NSTAGE; ++k) mbar_init(bar0 + 8 * k);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int t = t0; t < t0 + PREF && t < t1; ++t) issue(t);
+
+  // residual geometry: pair pc = columns c, c + 1 (c = cstart + 2 pc, odd);
+  // the last pair has no columns
+  const bool active = pc < UNPAIR - 1;
+  const int c = cstart + 2 * pc;
+  const float2 mxC = make_float2(active && c >= 1 && c <= n - 1 ? 1.f : 0.f,
+                                 active && c + 1 >= 1 && c + 1 <= n - 1 ? 1.f : 0.f);
+  const int rc0 = strip * URCB + min(strip, URCX);
+  const int ncrows = URCB + (strip < URCX ? 1 : 0);
+  float myC[URC];
+#pragma unroll
+  for (int i = 0; i < URC; ++i) {
+    const int y = 3 * Jy0 - 2 + rc0 + i;
+    myC[i] = (i < ncrows && y >= 1 && y <= n - 1) ? 1.f : 0.f;
+  }
+  const float2 ac2 = f2(p.a_c), ae2 = f2(p.a_e), ak2 = f2(p.a_k);
+  const float2 neg1 = f2(-1.f);
+  float2 PR[URC], YR[URC];
+#pragma unroll
+  for (int i = 0; i < URC; ++i) PR[i] = YR[i] = f2(0.f);
+  float accR[2] = {0.f, 0.f}, accB[2] = {0.f, 0.f};
+  // restriction geometry: coarse column tid
+  const bool hasJ = tid < UNJ;
+  const int cjx = tid % UBJX, cjy = tid / UBJX;
+  const int Jx = Jx0 + cjx, Jy = Jy0 + cjy;
+  const bool outJ = hasJ && Jx >= 1 && Jx <= nc - 1 && Jy >= 1 && Jy <= nc - 1;
+
+  const int tEnd = UPE ? t1 + 1 : t1;
+  for (int t = t0; t < tEnd; ++t) {
+    __syncthreads();
+    if (s_fail) break;
+    if (tid == 0 && t + PREF < t1) issue(t + PREF);
+    const int k = (t - t0) % NSTAGE;
+    if (t < t1 && !mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
+      s_fail = t - t0 + 1;
+      if (atomicCAS(p.fault, 0, 1) == 0) {
+        p.fault_info[0] = 10 + MODE;
+        p.fault_info[1] = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        p.fault_info[2] = t - t0;
+        p.fault_info[3] = k;
+        p.fault_info[4] = ((t - t0) / NSTAGE) & 1;
+        p.fault_info[5] = t;
+        p.fault_info[6] = tid;
+        p.fault_info[7] = t1 - t0;
+      }
+    }
+    const float* sE = smem + k * 2 * UPLANE_F;
+    const float* sRhs = sE + UPLANE_F;
+    const int r = UPE ? t - 2 : t;                      // plane restricted in this step
     const float* wbase;
     int pitch;
-    if (MODE == SWEEP_UPE) {
+    if (UPE) {
+      // residual of plane t - 1 into sR[(t - 1) & 1]
       const int rn = t - 1;
-      if (t < t1 && rn >= zC0 && rn < zC1) {
+      if (t < t1 && active) {
+        const bool store = rn >= zC0 && rn < zC1;
         const float zm = (rn >= 1 && rn <= n - 1) ? 1.f : 0.f;
-        const float* E = sE + (rc0 + 1) * BOXW + 2 * pc;
-        const float* Rh = sRhs + (rc0 + 2) * BOXW + 1 + 2 * pc;
-        float* sRn = sR + (rn & 1) * SR_F;
-        RowPair up = row_pair(E), ce = row_pair(E + BOXW);
+        const float* E = sE + rc0 * UBOXW + (c - 1 - xA);
+        const float* Rh = sRhs + (rc0 + 1) * UBOXW + (c - xA);
+        float* sRn = sR + (rn & 1) * USR_F;
+        RowPair up = row_pair(E), ce = row_pair(E + UBOXW);
 #pragma unroll
-        for (int i = 0; i < RC; ++i) {
+        for (int i = 0; i < URC; ++i) {
           if (i >= ncrows) break;
-          const RowPair dn = row_pair(E + (i + 2) * BOXW);
+          const RowPair dn = row_pair(E + (i + 2) * UBOXW);
           const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
-          const float2 Ae = add2(PR[i], q.Y);
-          const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
-          const float2 rho = mul2(fma2(Ae, neg1, rhs), mul2(mxC, f2(zm * myC[i])));
-          st2(sRn + (rc0 + i) * SR_P + 2 * pc, rho);
-          PR[i] = add2(q.W, YR[i]);
-          YR[i] = q.Y;
-          up = ce;
-          ce = dn;
-        }
-      } else if (t < t1) {
-        // planes before the first residual plane: only roll the stencil parts
-        const float* E = sE + (rc0 + 1) * BOXW + 2 * pc;
-        RowPair up = row_pair(E), ce = row_pair(E + BOXW);
-#pragma unroll
-        for (int i = 0; i < RC; ++i) {
-          if (i >= ncrows) break;
-          const RowPair dn = row_pair(E + (i + 2) * BOXW);
-          const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+          if (store) {
+            const float2 Ae = add2(PR[i], q.Y);
+            const float2 rhs = make_float2(Rh[i * UBOXW], Rh[i * UBOXW + 1]);
+            const float2 rho = mul2(fma2(Ae, neg1, rhs), mul2(mxC, f2(zm * myC[i])));
+            st2(sRn + (rc0 + i) * USR_P + 2 * pc, rho);
+          }
           PR[i] = add2(q.W, YR[i]);
           YR[i] = q.Y;
           up = ce;
           ce = dn;
         }
       }
-      // sR column j is box column j + 1, row j box row j + 2
-      wbase = sR + (r & 1) * SR_F;
-      pitch = SR_P;
+      // sR column j = absolute column cstart + j, row j = residual row j
+      wbase = sR + (r & 1) * USR_F + soff;
+      pitch = USR_P;
     } else {
       // UP: rho = rhs (zero outside the interior), read from the staged box
-      wbase = sRhs + 2 * BOXW + 1;
-      pitch = BOXW;
+      wbase = sRhs + UBOXW + (3 * Jx0 - 2 - xA);
+      pitch = UBOXW;
     }
     // ---- restriction and damping right-hand side of plane r -----------------
-    if (doC) {
+    if (hasJ && r >= zC0 && r < zC1) {
+      const float* w0 = wbase + (3 * cjy) * pitch + 3 * cjx;
+      float c0 = 0.f, l1 = 0.f, l2 = 0.f, p11 = 0.f, p12 = 0.f, p22 = 0.f;
 #pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        const int cj = tid + pass * NT;
-        if (cj >= NJ) break;
-        const int cjx = cj % BJX, cjy = cj / BJX;
-        // the 5x5 window of the coarse column (box columns 3 cjx + 2 .. + 6,
-        // rows 3 cjy + 2 .. + 6), summed per class of distances (|ox|, |oy|)
-        // from its centre: (0,0) (1,0) (2,0) (1,1) (1,2) (2,2)
-        const float* w0 = wbase + (3 * cjy) * pitch + 3 * cjx + 1;
-        float c0 = 0.f, l1 = 0.f, l2 = 0.f, p11 = 0.f, p12 = 0.f, p22 = 0.f;
-#pragma unroll
-        for (int oy = 0; oy < 5; ++oy) {
-          const float* row = w0 + oy * pitch;
-          const float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
-          if (oy == 2) {
-            c0 = v2;
-            l1 += v1 + v3;
-            l2 += v0 + v4;
-          } else if (oy == 1 || oy == 3) {
-            l1 += v2;
-            p11 += v1 + v3;
-            p12 += v0 + v4;
-          } else {
-            l2 += v2;
-            p12 += v1 + v3;
-            p22 += v0 + v4;
-          }
+      for (int oy = 0; oy < 5; ++oy) {
+        const float* row = w0 + oy * pitch;
+        const float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3], v4 = row[4];
+        if (oy == 2) {
+          c0 = v2;
+          l1 += v1 + v3;
+          l2 += v0 + v4;
+        } else if (oy == 1 || oy == 3) {
+          l1 += v2;
+          p11 += v1 + v3;
+          p12 += v0 + v4;
+        } else {
+          l2 += v2;
+          p12 += v1 + v3;
+          p22 += v0 + v4;
         }
-        const float rin = c0 + (2.f / 3.f) * l1 + (1.f / 3.f) * l2 + (4.f / 9.f) * p11 +
-                          (2.f / 9.f) * p12 + (1.f / 9.f) * p22;
-        const int jtop = (r + 2) / 3;  // r >= -2
+      }
+      const float rin = c0 + (2.f / 3.f) * l1 + (1.f / 3.f) * l2 + (4.f / 9.f) * p11 +
+                        (2.f / 9.f) * p12 + (1.f / 9.f) * p22;
+      const int jtop = (r + 2) / 3;  // r >= -2
 #pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          const int Jz = jtop - 1 + d;
-          const int oz = r - 3 * Jz;
-          if (oz < -2 || oz > 2 || Jz < Jz0 || Jz >= Jz1) continue;
-          const int az = oz < 0 ? -oz : oz;
-          const int slot = Jz & 1;
-          float aR = slot ? accR[pass][1] : accR[pass][0];
-          float aB = slot ? accB[pass][1] : accB[pass][0];
-          if (oz == -2) aR = aB = 0.f;
-          // d-linear restriction: weight (1 - |o|/3) per direction
-          aR = fmaf(1.f - (float)az * (1.f / 3.f), rin, aR);
-          const float* dz = p.dcls + 6 * az;
-          aB += dz[0] * c0 + dz[1] * l1 + dz[2] * l2 + dz[3] * p11 + dz[4] * p12 + dz[5] * p22;
-          if (slot) {
-            accR[pass][1] = aR;
-            accB[pass][1] = aB;
+      for (int d = 0; d < 2; ++d) {
+        const int Jz = jtop - 1 + d;
+        const int oz = r - 3 * Jz;
+        if (oz < -2 || oz > 2 || Jz < Jz0 || Jz >= Jz1) continue;
+        const int az = oz < 0 ? -oz : oz;
+        const int slot = Jz & 1;
+        float aR = slot ? accR[1] : accR[0];
+        float aB = slot ? accB[1] : accB[0];
+        if (oz == -2) aR = aB = 0.f;
+        aR = fmaf(1.f - (float)az * (1.f / 3.f), rin, aR);
+        const float* dz = p.dcls + 6 * az;
+        aB += dz[0] * c0 + dz[1] * l1 + dz[2] * l2 + dz[3] * p11 + dz[4] * p12 + dz[5] * p22;
+        if (slot) {
+          accR[1] = aR;
+          accB[1] = aB;
+        } else {
+          accR[0] = aR;
+          accB[0] = aB;
+        }
+        if (oz == 2 && outJ && Jz >= 1 && Jz <= nc - 1) {
+          const float bt = p.omega * aB;
+          const long long ci = ((long long)Jz * ncp1 + Jy) * ncp1 + Jx;
+          p.r_c[ci] = aR;
+          if (p.variant == V_JAC) {
+            p.bt_c[ci] = bt;
+            p.g_c[ci] = p.c_invd * (p.omega * aR - p.omega_t * bt);
           } else {
-            accR[pass][0] = aR;
-            accB[pass][0] = aB;
-          }
-          if (oz == 2) {
-            const int Jx = Jx0 + cjx, Jy = Jy0 + cjy;
-            if (Jx >= 1 && Jx <= nc - 1 && Jy >= 1 && Jy <= nc - 1 && Jz >= 1 &&
-                Jz <= nc - 1) {
-              const float bt = p.omega * aB;
-              const long long ci = ((long long)Jz * ncp1 + Jy) * ncp1 + Jx;
-              p.r_c[ci] = aR;
-              if (p.variant == V_JAC) {
-                p.bt_c[ci] = bt;
-                p.g_c[ci] = p.c_invd * (p.omega * aR - p.omega_t * bt);
-              } else {
-                p.bt_c[ci] = 0.f;
-                p.g_c[ci] = p.gscale * p.omega * p.c_invd * aR;
-              }
-            }
+            p.bt_c[ci] = 0.f;
+            p.g_c[ci] = p.gscale * p.omega * p.c_invd * aR;
           }
         }
       }
@@ -559,8 +608,6 @@ __global__ void __launch_bounds__(NT, MINB)
   __syncthreads();
   if (s_fail && tid == 0) {
     atomicExch(p.fault, 1);
-    // let the copies still in flight (steps tf .. tf + PREF) land before the
-    // block's shared memory is released
     const int tf = t0 + s_fail - 1;
     for (int tt = tf; tt <= tf + PREF && tt < t1; ++tt) {
       const uint32_t bar = bar0 + 8 * ((tt - t0) % NSTAGE);
@@ -690,7 +737,6 @@ __global__ void k_scale(const double* __restrict__ b, double* __restrict__ bq, l
 
 }  // namespace
 
-size_t sweep3_smem_bytes() { return SMEM_BYTES; }
 
 bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Maps* maps) {
   void* fn = nullptr;
@@ -707,11 +753,14 @@ bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Ma
   const cuuint64_t np1 = (cuuint64_t)n + 1;
   const cuuint64_t dims[3] = {np1, np1, np1};
   const cuuint64_t strides[2] = {(cuuint64_t)ldx * 4, (cuuint64_t)ldx * np1 * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)kBoxH, 1};
+  const cuuint32_t box_down[3] = {(cuuint32_t)kBoxW, (cuuint32_t)kBoxH, 1};
+  const cuuint32_t box_up[3] = {(cuuint32_t)kUpBoxW, (cuuint32_t)kUpBoxH, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  float* bases[3] = {e0, e1, rhs};
-  CUtensorMap* outs[3] = {&maps->e[0], &maps->e[1], &maps->rhs};
-  for (int i = 0; i < 3; ++i) {
+  float* bases[6] = {e0, e1, rhs, e0, e1, rhs};
+  CUtensorMap* outs[6] = {&maps->e[0],    &maps->e[1],    &maps->rhs,
+                          &maps->e_up[0], &maps->e_up[1], &maps->rhs_up};
+  for (int i = 0; i < 6; ++i) {
+    const cuuint32_t* box = i < 3 ? box_down : box_up;
     if (encode(outs[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, bases[i], dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -723,64 +772,51 @@ bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Ma
 
 void sweep3_grid(int nc, int zc, dim3* grid) {
   const int ncp1 = nc + 1;
-  *grid = dim3((ncp1 + BJX - 1) / BJX, (ncp1 + BJY - 1) / BJY, (ncp1 + zc - 1) / zc);
+  *grid = dim3((ncp1 + UBJX - 1) / UBJX, (ncp1 + UBJY - 1) / UBJY, (ncp1 + zc - 1) / zc);
 }
 
 void sweep3_grid_down(int nc, int zc, dim3* grid) {
   const int ncp1 = nc + 1;
   *grid = dim3((3 * nc + 63) / 64, (ncp1 + BJY - 1) / BJY, (ncp1 + zc - 1) / zc);
 }
-// threads and blocks per SM of each mode
-template <int MODE>
-struct Shape;
-template <>
-struct Shape<SWEEP_UP> {
-  static constexpr int NT = 256, MINB = 3;
-};
-template <>
-struct Shape<SWEEP_UPE> {
-  static constexpr int NT = 256, MINB = 3;
-};
-template <>
-struct Shape<SWEEP_DOWN> {
-  static constexpr int NT = 128, MINB = 3;
-};
-template <>
-struct Shape<SWEEP_DOWNU> {
-  static constexpr int NT = 128, MINB = 3;
-};
+// threads and blocks per SM of the down-passes
+constexpr int kDownNT = 128, kDownMinB = 3;
 
-template <int MODE>
-static bool prepare_mode() {
-  using S = Shape<MODE>;
-  return cudaFuncSetAttribute(k_sweep3<MODE, S::NT, S::MINB>,
+bool sweep3_prepare() {
+  return cudaFuncSetAttribute(k_up3<SWEEP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)USMEM_BYTES) == cudaSuccess &&
+         cudaFuncSetAttribute(k_up3<SWEEP_UPE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)USMEM_BYTES) == cudaSuccess &&
+         cudaFuncSetAttribute(k_down3<SWEEP_DOWN, kDownNT, kDownMinB>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SMEM_BYTES) == cudaSuccess &&
+         cudaFuncSetAttribute(k_down3<SWEEP_DOWNU, kDownNT, kDownMinB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SMEM_BYTES) == cudaSuccess;
 }
 
-bool sweep3_prepare() {
-  return prepare_mode<SWEEP_UP>() && prepare_mode<SWEEP_UPE>() && prepare_mode<SWEEP_DOWN>() &&
-         prepare_mode<SWEEP_DOWNU>();
-}
-
-template <int MODE>
-static void launch_mode(const Sweep3Params& p, const Sweep3Maps& maps, int ein, cudaStream_t s) {
-  using S = Shape<MODE>;
+void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
+                   cudaStream_t s) {
   dim3 grid;
-  if (MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU)
+  if (mode == SWEEP_DOWN || mode == SWEEP_DOWNU)
     sweep3_grid_down(p.nc, p.zc_down, &grid);
   else
     sweep3_grid(p.nc, p.zc, &grid);
-  k_sweep3<MODE, S::NT, S::MINB><<<grid, S::NT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
-}
-
-void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
-                   cudaStream_t s) {
   switch (mode) {
-    case SWEEP_UP: launch_mode<SWEEP_UP>(p, maps, ein, s); break;
-    case SWEEP_UPE: launch_mode<SWEEP_UPE>(p, maps, ein, s); break;
-    case SWEEP_DOWN: launch_mode<SWEEP_DOWN>(p, maps, ein, s); break;
-    default: launch_mode<SWEEP_DOWNU>(p, maps, ein, s); break;
+    case SWEEP_UP:
+      k_up3<SWEEP_UP><<<grid, UNT, USMEM_BYTES, s>>>(p, maps.e_up[ein], maps.rhs_up);
+      break;
+    case SWEEP_UPE:
+      k_up3<SWEEP_UPE><<<grid, UNT, USMEM_BYTES, s>>>(p, maps.e_up[ein], maps.rhs_up);
+      break;
+    case SWEEP_DOWN:
+      k_down3<SWEEP_DOWN, kDownNT, kDownMinB>
+          <<<grid, kDownNT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
+      break;
+    default:
+      k_down3<SWEEP_DOWNU, kDownNT, kDownMinB>
+          <<<grid, kDownNT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
+      break;
   }
 }
 

@@ -12,11 +12,13 @@ namespace adafac {
 // DOWN: down-pass; DOWNU: last down-pass (u += e, the other buffer zeroed)
 enum SweepMode { SWEEP_UP = 0, SWEEP_UPE = 1, SWEEP_DOWN = 2, SWEEP_DOWNU = 3 };
 
-// coarse columns per block of the up-passes (x, y); the z extent is a launch
-// parameter
-constexpr int kSweepBJX = 20, kSweepBJY = 8;
-// staged box of a plane: x from 3 J0x - 4 (a 16-byte boundary), 68 x 30 floats
-constexpr int kBoxW = 3 * kSweepBJX + 8, kBoxH = 3 * kSweepBJY + 6;
+// down-passes: 64 fine columns x 3 kSweepBJY rows per block, staged box
+// 68 x 30 floats (x origin 64 bx - 4, a 16-byte boundary)
+constexpr int kSweepBJY = 8;
+constexpr int kBoxW = 68, kBoxH = 3 * kSweepBJY + 6;
+// up-passes: 41 x 4 coarse columns per block, staged box 132 x 16 floats
+constexpr int kUpBJX = 41, kUpBJY = 4;
+constexpr int kUpBoxW = 132, kUpBoxH = 16;
 
 struct Sweep3Params {
   int n = 0, nc = 0, zc = 0;       // fine cells, coarse cells, coarse planes per block
@@ -59,18 +61,19 @@ struct Refine3Params {
 
 // Tensor maps of the FP32 fine arrays for the staged loads.
 struct Sweep3Maps {
-  CUtensorMap e[2];
+  CUtensorMap e[2];      // down-pass boxes (kBoxW x kBoxH)
   CUtensorMap rhs;
+  CUtensorMap e_up[2];   // up-pass boxes (kUpBoxW x kUpBoxH)
+  CUtensorMap rhs_up;
 };
 
 // Encodes the tensor maps (host; false when the driver entry point is missing).
 bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Maps* maps);
-size_t sweep3_smem_bytes();
 // Allows the sweeps' dynamic shared memory (once per process and device).
 bool sweep3_prepare();
 void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
                    cudaStream_t s);
-void sweep3_grid(int nc, int zc, dim3* grid);       // up-passes
+void sweep3_grid(int nc, int zc, dim3* grid);       // up-passes (41 x 4 coarse columns)
 void sweep3_grid_down(int nc, int zc, dim3* grid);  // down-passes (64-column tiles)
 int refine3_blocks(int n, int zc);
 void launch_refine3(const Refine3Params& p, cudaStream_t s);
