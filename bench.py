@@ -379,6 +379,89 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def run_serving(count: int, seed: int = 1903):
+    """The serving configuration: a seeded stream of ``count`` solves (80 % 2-D
+    depth 3..6, 20 % 3-D depth 3..5, random-block eps 1 / 1e-2, BoxMG, mixed
+    precision, to 1e-8) through the request server.  First the whole stream at
+    once (saturated throughput), then the same stream with Poisson arrivals at
+    0.8 x that throughput (p50 / p99 latency from submission to the solution in
+    host memory).  The comparator solves every request alone with plain FP64
+    cycles on a single handle, one after another (setup + solve + copy of u)."""
+    import torch
+    from paper_1903_10367_gb300 import adafac
+    reqs = wl.serving_requests(count, seed)
+    om = adafac.default_options(transfer="boxmg", precision="mixed")
+    o64 = adafac.default_options(transfer="boxmg", precision="fp64")
+    free, _ = torch.cuda.mem_get_info()
+    pool = int(min(0.6 * free, 96 << 30))
+    srv = adafac.Server(pool, n_streams=32, max_running=32)
+
+    def submit(r):
+        return srv.submit(r.dim, r.depth, r.eps, r.f, om, 1e-8, 3000)
+
+    def drain(tickets):
+        while any(srv.poll(t)["state"] in ("pending", "running") for t in tickets):
+            time.sleep(0.0005)
+        infos = [srv.poll(t) for t in tickets]
+        for t in tickets:
+            srv.fetch(t)
+        return infos
+
+    drain([submit(r) for r in reqs[:8]])          # warm-up
+    t0 = time.perf_counter()
+    infos = drain([submit(r) for r in reqs])
+    t_sat = time.perf_counter() - t0
+    ok = all(i["state"] == "done" and i["rel"] <= 1e-8 for i in infos)
+    lam_sat = count / t_sat
+    upd = sum(i["cycles"] * sum(wl.Workload("r", r.dim, r.depth, "blocks").level_dofs())
+              for i, r in zip(infos, reqs))
+    lam = 0.8 * lam_sat
+    start = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        target = start + r.arrival / lam
+        while True:
+            dt = target - time.perf_counter()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.0005))
+        tickets.append(submit(r))
+    infos_open = drain(tickets)
+    t_open = time.perf_counter() - start
+    srv.close()
+    lat = np.array([i["latency_ms"] for i in infos_open])
+    ok = ok and all(i["state"] == "done" and i["rel"] <= 1e-8 for i in infos_open)
+    single = []
+    for r in reqs:
+        t1 = time.perf_counter()
+        S = adafac.Solver(r.dim, r.depth, r.eps, r.f, o64)
+        S.solve(1e-8, 3000)
+        S.solution()
+        S.close()
+        single.append(1e3 * (time.perf_counter() - t1))
+    single = np.array(single)
+    return {
+        "requests": count, "seed": seed,
+        "mix": "80% 2-D depth U{3..6}, 20% 3-D depth U{3..5}; eps blocks of level-min(3, depth-1) "
+               "cells, 1 or 1e-2; f = 1; BoxMG + Galerkin; to 1e-8",
+        "all_converged": bool(ok),
+        "saturated_requests_per_s": lam_sat,
+        "saturated_vertex_updates_per_s": upd / t_sat,
+        "offered_requests_per_s": lam, "offered_load": "0.8 x saturated throughput",
+        "open_loop_s": t_open,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()),
+        "server": {"pool_bytes": pool, "streams": 32, "max_running": 32,
+                   "precision": "mixed (FP32 cycles, FP64 refinement)"},
+        "fp64_single_instance": {
+            "requests_per_s": count / (single.sum() / 1e3),
+            "p50_ms": float(np.percentile(single, 50)), "p99_ms": float(np.percentile(single, 99)),
+            "mean_ms": float(single.mean()),
+            "how": "each request alone: setup + FP64 solve to 1e-8 + copy of u, back to back"},
+        "throughput_vs_fp64_single": lam_sat / (count / (single.sum() / 1e3)),
+    }
+
+
 def _traffic_from_profile(kind, w):
     """DRAM bytes (read + write) per launch of this kernel from the committed
     ncu summary (profiles/traffic.json), or None when the summary was taken on
