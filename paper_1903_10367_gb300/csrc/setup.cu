@@ -63,6 +63,49 @@ __device__ double fine_stencil_entry(const LevelView<double>& lv, const int* c, 
   return lv.hfac * acc;
 }
 
+// All 3^D stencil entries of vertex c at once: every cell a containing c (as
+// its corner a) adds eps_cell K_ref(a, b) to the entry of the offset b - a of
+// each of its corners b (Sec. 2.1).  Equals fine_stencil_entry for every s.
+template <int D>
+__device__ void fine_stencil_all(const LevelView<double>& lv, const int* c, double* st) {
+  constexpr int NS = ipow_c(3, D), NC = 1 << D;
+  if (lv.opkind == OP_UNIFORM) {
+    for (int s = 0; s < NS; ++s) st[s] = lv.cst[s];
+    return;
+  }
+  if (lv.opkind == OP_STORED) {
+    const long long v = encode<D>(c, lv.np1);
+    for (int s = 0; s < NS; ++s) st[s] = lv.st[(long long)s * lv.V + v];
+    return;
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) st[s] = 0.0;
+#pragma unroll
+  for (int a = 0; a < NC; ++a) {
+    int cell[D];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      cell[j] = c[j] - ((a >> j) & 1);
+      if (cell[j] < 0 || cell[j] >= lv.n) ok = false;
+    }
+    if (!ok) continue;
+    const double e = lv.eps[encode<D>(cell, lv.n)];
+#pragma unroll
+    for (int b = 0; b < NC; ++b) {
+      int s = 0, mul = 1;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        s += (((b >> j) & 1) - ((a >> j) & 1) + 1) * mul;
+        mul *= 3;
+      }
+      st[s] += e * kref<D, double>(__popc(a ^ b));
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) st[s] *= lv.hfac;
+}
+
 template <int D>
 __global__ void k_fine_invdiag(LevelView<double> lv, double* __restrict__ invd) {
   constexpr int centre = (ipow_c(3, D) - 1) / 2;
@@ -74,8 +117,10 @@ __global__ void k_fine_invdiag(LevelView<double> lv, double* __restrict__ invd) 
   }
 }
 
-// Solves M x = rhs (m <= 8) by Gaussian elimination with partial pivoting.
-__device__ void small_solve(double* M, double* rhs, int m) {
+// Solves M X = R for NR right-hand sides (m <= 8 unknowns; R is m x NR,
+// row-major with stride NR) by Gaussian elimination with partial pivoting.
+template <int NR>
+__device__ void small_solve_multi(double* M, double* R, int m) {
   for (int k = 0; k < m; ++k) {
     int p = k;
     double best = fabs(M[k * 8 + k]);
@@ -90,31 +135,38 @@ __device__ void small_solve(double* M, double* rhs, int m) {
         M[k * 8 + j] = M[p * 8 + j];
         M[p * 8 + j] = t;
       }
-      const double t = rhs[k];
-      rhs[k] = rhs[p];
-      rhs[p] = t;
+      for (int r = 0; r < NR; ++r) {
+        const double t = R[k * NR + r];
+        R[k * NR + r] = R[p * NR + r];
+        R[p * NR + r] = t;
+      }
     }
-    const double piv = M[k * 8 + k];
+    const double inv = 1.0 / M[k * 8 + k];
     for (int i = k + 1; i < m; ++i) {
-      const double f = M[i * 8 + k] / piv;
+      const double f = M[i * 8 + k] * inv;
       for (int j = k; j < m; ++j) M[i * 8 + j] -= f * M[k * 8 + j];
-      rhs[i] -= f * rhs[k];
+      for (int r = 0; r < NR; ++r) R[i * NR + r] -= f * R[k * NR + r];
     }
   }
   for (int k = m - 1; k >= 0; --k) {
-    double s = rhs[k];
-    for (int j = k + 1; j < m; ++j) s -= M[k * 8 + j] * rhs[j];
-    rhs[k] = s / M[k * 8 + k];
+    const double inv = 1.0 / M[k * 8 + k];
+    for (int r = 0; r < NR; ++r) {
+      double t = R[k * NR + r];
+      for (int j = k + 1; j < m; ++j) t -= M[k * 8 + j] * R[j * NR + r];
+      R[k * NR + r] = t * inv;
+    }
   }
 }
 
 // BoxMG prolongation for 3:1 coarsening (Sec. 2.4): one thread per coarse
-// cell.  For every corner e: value 1 at the c-point of e, 0 at the others;
-// gamma-points on the cell's edges (and, in 3-D, faces) solve the stencil
-// lumped along the sub-face normals with the rim as data; f-points solve the
-// full stencil.  Sub-faces on the domain boundary keep zeros.  Writes the
-// weights of the fine vertices the cell owns (local offset < 3, or = 3 on the
-// last cell of a row).
+// cell, all 2^D corners e at once.  For every corner e: value 1 at the c-point
+// of e, 0 at the other corners; gamma-points on the cell's edges (and, in
+// 3-D, faces) solve the stencil lumped along the sub-face normals with the rim
+// as data; f-points solve the full stencil.  The matrix of a sub-face does not
+// depend on e: it is assembled and factored once and solved for the 2^D
+// right-hand sides.  Sub-faces on the domain boundary, and corners on the
+// coarse boundary, keep zeros.  Writes the weights of the fine vertices the
+// cell owns (local offset < 3, or = 3 on the last cell of a row).
 template <int D>
 __global__ void __launch_bounds__(64) k_boxmg(LevelView<double> fine, double* __restrict__ P, int n_c) {
   constexpr int NC = 1 << D;
@@ -126,116 +178,118 @@ __global__ void __launch_bounds__(64) k_boxmg(LevelView<double> fine, double* __
   if (E >= total) return;
   int ec[D];
   decode<D>(E, n_c, ec);
+  double v[NP * NC];  // v[p * NC + e]: P e at closure point p
+  for (int i = 0; i < NP * NC; ++i) v[i] = 0.0;
   for (int e = 0; e < NC; ++e) {
-    // coarse boundary corner: weights stay zero
+    // corners on the coarse boundary carry no unknown: their weights stay zero
     bool cb = false;
+    int cp[D];
     for (int j = 0; j < D; ++j) {
       const int J = ec[j] + ((e >> j) & 1);
       if (J == 0 || J == n_c) cb = true;
+      cp[j] = 3 * ((e >> j) & 1);
     }
-    double v[NP];
-    for (int p = 0; p < NP; ++p) v[p] = 0.0;
-    if (!cb) {
-      int cp[D];
-      for (int j = 0; j < D; ++j) cp[j] = 3 * ((e >> j) & 1);
-      v[encode<D>(cp, 4)] = 1.0;
-      for (int nfree = 1; nfree <= D; ++nfree) {
-        for (int F = 0; F < NC; ++F) {
-          if (__popc(F) != nfree) continue;
-          const int nfix = D - nfree;
-          for (int fb = 0; fb < (1 << nfix); ++fb) {
-            // fixed coordinates of the bounding dims
-            int lfix[D];
-            bool on_bnd = false;
-            int k = 0;
+    if (!cb) v[encode<D>(cp, 4) * NC + e] = 1.0;
+  }
+  for (int nfree = 1; nfree <= D; ++nfree) {
+    for (int F = 0; F < NC; ++F) {
+      if (__popc(F) != nfree) continue;
+      const int nfix = D - nfree;
+      for (int fb = 0; fb < (1 << nfix); ++fb) {
+        // fixed coordinates of the bounding dims
+        int lfix[D];
+        bool on_bnd = false;
+        int k = 0;
+        for (int j = 0; j < D; ++j) {
+          lfix[j] = 0;
+          if (!((F >> j) & 1)) {
+            lfix[j] = ((fb >> k) & 1) ? 3 : 0;
+            ++k;
+            if ((lfix[j] == 0 && ec[j] == 0) || (lfix[j] == 3 && ec[j] == n_c - 1)) on_bnd = true;
+          }
+        }
+        if (on_bnd) continue;  // zeros
+        const int m = 1 << nfree;
+        double M[64], R[8 * NC];
+        for (int i = 0; i < 64; ++i) M[i] = 0.0;
+        for (int i = 0; i < 8 * NC; ++i) R[i] = 0.0;
+        for (int p = 0; p < m; ++p) {
+          // unknown point p: free coords 1 or 2 by the bits of p
+          int lp[D];
+          int q = 0;
+          for (int j = 0; j < D; ++j) {
+            if ((F >> j) & 1) {
+              lp[j] = 1 + ((p >> q) & 1);
+              ++q;
+            } else {
+              lp[j] = lfix[j];
+            }
+          }
+          int fpc[D];
+          for (int j = 0; j < D; ++j) fpc[j] = 3 * ec[j] + lp[j];
+          double st[NS];
+          fine_stencil_all<D>(fine, fpc, st);
+          // collapsed stencil: offsets along the fixed dims fold onto the sub-face
+          for (int s = 0; s < NS; ++s) {
+            int o[D], t = s;
             for (int j = 0; j < D; ++j) {
-              lfix[j] = 0;
-              if (!((F >> j) & 1)) {
-                lfix[j] = ((fb >> k) & 1) ? 3 : 0;
-                ++k;
-                if ((lfix[j] == 0 && ec[j] == 0) || (lfix[j] == 3 && ec[j] == n_c - 1)) on_bnd = true;
+              o[j] = t % 3 - 1;
+              t /= 3;
+            }
+            int nb[D];
+            for (int j = 0; j < D; ++j) nb[j] = ((F >> j) & 1) ? lp[j] + o[j] : lp[j];
+            const double coef = st[s];
+            bool unk = true;
+            int qi = 0, qq = 0;
+            for (int j = 0; j < D; ++j) {
+              if ((F >> j) & 1) {
+                if (nb[j] < 1 || nb[j] > 2) unk = false;
+                qi |= (nb[j] - 1) << qq;
+                ++qq;
               }
             }
-            if (on_bnd) continue;  // zeros
-            const int m = 1 << nfree;
-            double M[64], rhs[8];
-            for (int i = 0; i < 64; ++i) M[i] = 0.0;
-            for (int p = 0; p < m; ++p) {
-              // unknown point p: free coords 1 or 2 by the bits of p
-              int lp[D];
-              int q = 0;
-              for (int j = 0; j < D; ++j) {
-                if ((F >> j) & 1) {
-                  lp[j] = 1 + ((p >> q) & 1);
-                  ++q;
-                } else {
-                  lp[j] = lfix[j];
-                }
-              }
-              int fpc[D];
-              for (int j = 0; j < D; ++j) fpc[j] = 3 * ec[j] + lp[j];
-              rhs[p] = 0.0;
-              // collapsed stencil: sum over offsets along the fixed dims
-              for (int s = 0; s < NS; ++s) {
-                int o[D], t = s;
-                for (int j = 0; j < D; ++j) {
-                  o[j] = t % 3 - 1;
-                  t /= 3;
-                }
-                int nb[D];
-                for (int j = 0; j < D; ++j) nb[j] = ((F >> j) & 1) ? lp[j] + o[j] : lp[j];
-                const double coef = fine_stencil_entry<D>(fine, fpc, s);
-                // is the neighbour an unknown of this sub-face?
-                bool unk = true;
-                int qi = 0, qq = 0;
-                for (int j = 0; j < D; ++j) {
-                  if ((F >> j) & 1) {
-                    if (nb[j] < 1 || nb[j] > 2) unk = false;
-                    qi |= (nb[j] - 1) << qq;
-                    ++qq;
-                  }
-                }
-                if (unk) {
-                  M[p * 8 + qi] += coef;
-                } else {
-                  rhs[p] -= coef * v[encode<D>(nb, 4)];
-                }
-              }
-            }
-            small_solve(M, rhs, m);
-            for (int p = 0; p < m; ++p) {
-              int lp[D];
-              int q = 0;
-              for (int j = 0; j < D; ++j) {
-                if ((F >> j) & 1) {
-                  lp[j] = 1 + ((p >> q) & 1);
-                  ++q;
-                } else {
-                  lp[j] = lfix[j];
-                }
-              }
-              v[encode<D>(lp, 4)] = rhs[p];
+            if (unk) {
+              M[p * 8 + qi] += coef;
+            } else {
+              const double* vn = v + encode<D>(nb, 4) * NC;
+              for (int e = 0; e < NC; ++e) R[p * NC + e] -= coef * vn[e];
             }
           }
         }
+        small_solve_multi<NC>(M, R, m);
+        for (int p = 0; p < m; ++p) {
+          int lp[D];
+          int q = 0;
+          for (int j = 0; j < D; ++j) {
+            if ((F >> j) & 1) {
+              lp[j] = 1 + ((p >> q) & 1);
+              ++q;
+            } else {
+              lp[j] = lfix[j];
+            }
+          }
+          double* vp = v + encode<D>(lp, 4) * NC;
+          for (int e = 0; e < NC; ++e) vp[e] = R[p * NC + e];
+        }
       }
     }
-    // owned fine vertices
-    const int np1f = 3 * n_c + 1;
-    long long Vf = 1;
-    for (int j = 0; j < D; ++j) Vf *= np1f;
-    for (int p = 0; p < NP; ++p) {
-      int lc[D], fc[D];
-      decode<D>(p, 4, lc);
-      bool owned = true, fbnd = false;
-      for (int j = 0; j < D; ++j) {
-        if (lc[j] == 3 && ec[j] != n_c - 1) owned = false;
-        fc[j] = 3 * ec[j] + lc[j];
-        if (fc[j] == 0 || fc[j] == 3 * n_c) fbnd = true;
-      }
-      if (!owned) continue;
-      P[(long long)e * Vf + encode<D>(fc, np1f)] = fbnd ? 0.0 : v[p];
+  }
+  // owned fine vertices
+  const int np1f = 3 * n_c + 1;
+  long long Vf = 1;
+  for (int j = 0; j < D; ++j) Vf *= np1f;
+  for (int p = 0; p < NP; ++p) {
+    int lc[D], fc[D];
+    decode<D>(p, 4, lc);
+    bool owned = true, fbnd = false;
+    for (int j = 0; j < D; ++j) {
+      if (lc[j] == 3 && ec[j] != n_c - 1) owned = false;
+      fc[j] = 3 * ec[j] + lc[j];
+      if (fc[j] == 0 || fc[j] == 3 * n_c) fbnd = true;
     }
+    if (!owned) continue;
+    const long long fv = encode<D>(fc, np1f);
+    for (int e = 0; e < NC; ++e) P[(long long)e * Vf + fv] = fbnd ? 0.0 : v[p * NC + e];
   }
 }
 
