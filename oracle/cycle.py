@@ -267,16 +267,26 @@ def cycle(H: Hierarchy, u: np.ndarray, variant: str = "jac", form: str = "cs",
         parts["ct"] = ct
     elif variant not in ("additive", "exp"):
         raise ValueError(variant)
-    u_new = zero_boundary(u + du)
+    # boundary vertices carry Dirichlet data, not unknowns (Sec. 2.1): the
+    # update acts on the interior and the iterate keeps its boundary values
+    u_new = u + zero_boundary(du)
     if return_parts:
         return u_new, parts
     return u_new
 
 
+def with_boundary(g: np.ndarray) -> np.ndarray:
+    """Initial iterate for Dirichlet data g: g on the boundary, 0 inside (the
+    setups of Sec. 5 prescribe u = 1 on x_2 = 0 and u = 0 elsewhere on the
+    boundary)."""
+    return g - zero_boundary(np.array(g, dtype=np.float64))
+
+
 def solve(H: Hierarchy, u0=None, tol: float = 1e-8, max_cycles: int = 500,
           **kw):
     """Cycles until ||r_n||_h / ||r_0||_h <= tol.  Returns (u, history) where
-    history[n] is the normalised residual of iterate n (history[0] = 1)."""
+    history[n] is the normalised residual of iterate n (history[0] = 1).  The
+    boundary entries of u0 are the Dirichlet values (zero by default)."""
     u = np.zeros_like(H.b) if u0 is None else u0.copy()
     r0 = residual_norm(H, residual(H, H.L, u, H.b))
     hist = [1.0]

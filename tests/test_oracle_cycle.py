@@ -251,3 +251,43 @@ def test_plain_additive_overshoot_grows_with_the_number_of_levels():
     for L in (3, 4):
         assert lam["jac", L] < lam["additive", L] - 0.2
         assert lam["pi", L] < 1.0
+
+
+# ---------------------------------------------------------------------------
+# non-zero Dirichlet data (the setups of Sec. 5: u = 1 on x_2 = 0)
+
+@pytest.mark.parametrize("d,L,transfer_kind", [(2, 3, "dlinear"), (2, 3, "boxmg"), (3, 2, "dlinear")])
+def test_linear_boundary_data_give_the_linear_solution(d, L, transfer_kind):
+    # d-linear elements contain the linear functions and, for constant eps and
+    # f = 0, A applied to a linear function vanishes at interior vertices:
+    # the discrete solution is the linear function itself
+    n = 3 ** L
+    coords = np.meshgrid(*([np.arange(n + 1) / n] * d), indexing="ij")
+    lin = 0.3 + sum((k + 1) * 0.7 * c for k, c in enumerate(coords))
+    H = cycle.build_hierarchy(d, L, [2.5], True, np.zeros((n + 1,) * d), transfer_kind)
+    for variant in ("jac", "pi", "additive"):
+        u, hist = cycle.solve(H, cycle.with_boundary(lin), variant=variant, tol=1e-13,
+                              max_cycles=3000)
+        assert hist[-1] <= 1e-13
+        np.testing.assert_allclose(u, lin, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("d,L,transfer_kind", [(2, 3, "boxmg"), (3, 2, "boxmg")])
+def test_boundary_data_match_a_lifted_direct_solve(d, L, transfer_kind):
+    # u_I = A_II^-1 (b_I - A_IB g_B) with the brute-force stiffness matrix
+    rng = np.random.default_rng(5)
+    n = 3 ** L
+    eps = rng.choice([1.0, 1e-3], size=(n,) * d)
+    g = np.zeros((n + 1,) * d)
+    g[0] = 1.0  # u = 1 on the face x_2 = 0 (first array axis), 0 elsewhere
+    f = np.ones((n + 1,) * d)
+    H = cycle.build_hierarchy(d, L, eps, False, f, transfer_kind)
+    Afull = _brute.stiffness_dense(d, n, eps)
+    fin = _brute.interior_mask(d, n)
+    gb = cycle.with_boundary(g).ravel()
+    rhs = fem.interior(H.b).ravel() - Afull[np.ix_(fin, ~fin)] @ gb[~fin]
+    x = np.linalg.solve(Afull[np.ix_(fin, fin)], rhs)
+    u, hist = cycle.solve(H, cycle.with_boundary(g), variant="jac", tol=1e-13, max_cycles=3000)
+    assert hist[-1] <= 1e-13
+    np.testing.assert_allclose(fem.interior(u).ravel(), x, rtol=1e-9, atol=1e-10)
+    np.testing.assert_array_equal(u - fem.zero_boundary(u.copy()), cycle.with_boundary(g))
