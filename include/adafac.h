@@ -152,16 +152,26 @@ adafac_status adafac_solve(adafac_handle h, double rel_tol, int max_cycles,
 adafac_status adafac_residual_norm(adafac_handle h, double* rel, double* abs);
 
 /* Copies the current fine-level iterate u ((3^L+1)^dim doubles including the
- * zero boundary) to dst (host if dst_on_device == 0, else device).
+ * boundary values) to dst (host if dst_on_device == 0, else device).
  * Synchronises. */
 adafac_status adafac_solution(adafac_handle h, double* dst, int dst_on_device);
 
 /* Sets the iterate u from src (same layout; boundary entries are ignored and
- * kept zero) and makes its residual the new r_0.  Synchronises. */
+ * keep the Dirichlet values) and makes its residual the new r_0.
+ * Synchronises. */
 adafac_status adafac_set_solution(adafac_handle h, const double* src,
                                   int src_on_device);
 
-/* Resets u = 0, r_0 := the next residual evaluated, and the history.
+/* Sets the Dirichlet values: the boundary entries of g ((3^L+1)^dim doubles,
+ * host if g_on_device == 0, else device; interior entries ignored) become
+ * the boundary of u and stay fixed; the interior of u is kept and its
+ * residual becomes the new r_0.  The setups of Sec. 5 prescribe u = 1 on
+ * x_2 = 0 and 0 elsewhere (setup starts with zero values).  Requires the
+ * correction-scheme form (INVALID_ARG for FAS).  Synchronises. */
+adafac_status adafac_set_boundary(adafac_handle h, const double* g, int g_on_device);
+
+/* Resets u = 0 inside (the Dirichlet values on the boundary), r_0 := the next
+ * residual evaluated, and the history.
  * Asynchronous (a device kernel resets the control block). */
 adafac_status adafac_reset(adafac_handle h);
 

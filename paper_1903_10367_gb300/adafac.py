@@ -76,6 +76,7 @@ _SIGNATURES = [
     ("adafac_residual_norm", _I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     ("adafac_solution", _I, [_P, _P, _I]),
     ("adafac_set_solution", _I, [_P, _P, _I]),
+    ("adafac_set_boundary", _I, [_P, _P, _I]),
     ("adafac_reset", _I, [_P]),
     ("adafac_get_field", _I, [_P, _I, _I, _P, _I, ctypes.POINTER(ctypes.c_size_t)]),
     ("adafac_history", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
@@ -254,6 +255,11 @@ class Solver:
             _check(self.lib.adafac_set_solution(self.h, _host_ptr(a), 0), self.h)
         else:
             _check(self.lib.adafac_set_solution(self.h, ctypes.c_void_p(u.data_ptr()), 1), self.h)
+
+    def set_boundary(self, g):
+        """Dirichlet values: the boundary entries of g (a (3^L+1)^dim array)."""
+        g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+        _check(self.lib.adafac_set_boundary(self.h, _host_ptr(g), 0), self.h)
 
     def reset(self):
         _check(self.lib.adafac_reset(self.h), self.h)

@@ -93,6 +93,7 @@ struct adafac_handle_s {
   float* e32b = nullptr;     // second correction buffer (ping-pong)
   int ebase = 0;             // which of e32 / e32b holds zeros at a step start
   double* bq = nullptr;      // b / alpha (3-D uniform path)
+  double* ub = nullptr;      // Dirichlet values on the boundary, zero inside
   long long e_elems = 0;     // floats of e32 / e32b / rhs32 (padded rows on the 3-D path)
   int npartials = 0;
   int ldx = 0;               // row stride of the padded FP32 fine arrays
@@ -230,6 +231,7 @@ void carve(adafac_handle h, Carver& cv) {
   }
   const long long Vf = h->lev[L].V;
   h->u = cv.take<double>(Vf);
+  h->ub = cv.take<double>(Vf);
   h->b = cv.take<double>(Vf);
   if (h->fast3) h->bq = cv.take<double>(Vf);
   if (!h->eps_scalar) {
@@ -821,20 +823,22 @@ adafac_status write_ctl_field(adafac_handle h, size_t offset, const F& value) {
   return ADAFAC_OK;
 }
 
-__global__ void k_mask_boundary2(double* u, int n) {
-  const int np1 = n + 1;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < (long long)np1 * np1;
-       v += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(v % np1), y = (int)(v / np1);
-    if (x == 0 || y == 0 || x == n || y == n) u[v] = 0.0;
-  }
-}
-__global__ void k_mask_boundary3(double* u, int n) {
+// Boundary vertices of u take the Dirichlet values of ub (interior ones keep
+// theirs): interior = false.  Interior vertices are zeroed and boundary ones
+// kept: interior = true (the masked copy of Dirichlet data).
+__global__ void k_boundary(double* u, const double* ub, int n, int D, int interior) {
   const long long np1 = n + 1;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < np1 * np1 * np1;
+  const long long V = D == 2 ? np1 * np1 : np1 * np1 * np1;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
        v += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(v % np1), y = (int)((v / np1) % np1), z = (int)(v / (np1 * np1));
-    if (x == 0 || y == 0 || z == 0 || x == n || y == n || z == n) u[v] = 0.0;
+    const int x = (int)(v % np1), y = (int)((v / np1) % np1);
+    const int z = D == 2 ? 1 : (int)(v / (np1 * np1));
+    const bool bnd = x == 0 || y == 0 || x == n || y == n || (D == 3 && (z == 0 || z == n));
+    if (interior) {
+      if (!bnd) u[v] = 0.0;
+    } else if (bnd) {
+      u[v] = ub ? ub[v] : 0.0;
+    }
   }
 }
 
@@ -1087,15 +1091,31 @@ adafac_status adafac_set_solution(adafac_handle h, const double* src, int src_on
                       src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess)
     return check_cuda(h, "copy iterate");
+  k_boundary<<<1024, 256, 0, h->stream>>>(h->u, h->ub, h->lev[h->L].n, h->D, 0);
+  return reset_control(h);
+}
+
+adafac_status adafac_set_boundary(adafac_handle h, const double* g, int g_on_device) {
+  if (!h || !g) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  if (h->opt.form == ADAFAC_FORM_FAS)
+    return fail(h, ADAFAC_ERR_INVALID_ARG,
+                "non-zero Dirichlet values need the correction-scheme form");
+  const size_t bytes = sizeof(double) * h->lev[h->L].V;
+  if (cudaMemcpyAsync(h->ub, g, bytes,
+                      g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess)
+    return check_cuda(h, "copy boundary values");
   const int n = h->lev[h->L].n;
-  if (h->D == 2) k_mask_boundary2<<<256, 256, 0, h->stream>>>(h->u, n);
-  else k_mask_boundary3<<<1024, 256, 0, h->stream>>>(h->u, n);
+  k_boundary<<<1024, 256, 0, h->stream>>>(h->ub, nullptr, n, h->D, 1);
+  k_boundary<<<1024, 256, 0, h->stream>>>(h->u, h->ub, n, h->D, 0);
   return reset_control(h);
 }
 
 adafac_status adafac_reset(adafac_handle h) {
   if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
-  cudaMemsetAsync(h->u, 0, sizeof(double) * h->lev[h->L].V, h->stream);
+  // u = 0 inside, the Dirichlet values on the boundary
+  cudaMemcpyAsync(h->u, h->ub, sizeof(double) * h->lev[h->L].V, cudaMemcpyDeviceToDevice,
+                  h->stream);
   return reset_control(h);
 }
 

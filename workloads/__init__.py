@@ -199,3 +199,49 @@ def serving_requests(count: int, seed: int = 1903, low: float = 1e-2):
         eps = eps_random_blocks(dim, depth, block, low, seed + 1 + i)
         out.append(ServingRequest(i, dim, depth, eps, constant_rhs(dim, depth), t))
     return out
+
+
+# ---------------------------------------------------------------------------
+# The setups of the paper's Sec. 5: f = 0, u = 1 on x_2 = 0 and u = 0 on the
+# rest of the boundary, eps = 1 or 10^-k / 10^k in one of three geometries.
+# Coordinates: x_1 is the last array axis (x), x_2 the one before (y); the
+# 3-D variants extend the 2-D geometry uniformly along z.
+
+def _cell_centres(dim: int, depth: int):
+    n = 3 ** depth
+    c1 = (np.arange(n) + 0.5) / n
+    return np.meshgrid(*([c1] * dim), indexing="ij")
+
+
+def bottom_boundary(dim: int, depth: int) -> np.ndarray:
+    """Dirichlet values: 1 at the vertices with x_2 = 0, 0 elsewhere."""
+    g = np.zeros((3 ** depth + 1,) * dim)
+    idx = [slice(None)] * dim
+    idx[dim - 2] = 0
+    g[tuple(idx)] = 1.0
+    return g
+
+
+def eps_halves(dim: int, depth: int, low: float) -> np.ndarray:
+    """eps = 1 for x_1 < 1/2, ``low`` for x_1 >= 1/2 (by cell centre; the split
+    does not coincide with the 3:1 mesh lines)."""
+    c = _cell_centres(dim, depth)
+    return np.where(c[dim - 1] < 0.5, 1.0, float(low))
+
+
+def eps_needle(dim: int, depth: int, high: float) -> np.ndarray:
+    """A line of width 0.02 with eps = ``high`` in eps = 1: the cells whose
+    centre lies within 0.01 of x_1 = 1/2 and below x_2 = 1/2 (the line starts
+    at the boundary x_2 = 0 and ends half-way into the domain)."""
+    c = _cell_centres(dim, depth)
+    inside = (np.abs(c[dim - 1] - 0.5) < 0.01) & (c[dim - 2] < 0.5)
+    return np.where(inside, float(high), 1.0)
+
+
+def eps_checkerboard(dim: int, depth: int, low: float) -> np.ndarray:
+    """Four regions separated by the lines x_2 = 5 x_1 - 2.5 and
+    x_2 = 0.2 x_1 + 0.5, eps = 1 and ``low`` in checkerboard fashion."""
+    c = _cell_centres(dim, depth)
+    x1, x2 = c[dim - 1], c[dim - 2]
+    s = (x2 - 5.0 * x1 + 2.5) * (x2 - 0.2 * x1 - 0.5)
+    return np.where(s > 0, 1.0, float(low))
