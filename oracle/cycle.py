@@ -93,10 +93,24 @@ def truncate_stencil(S_full: np.ndarray) -> np.ndarray:
     return S_full[tuple(slice(1, 6) for _ in range(S_full.ndim))].copy()
 
 
+def coarse_eps(eps: np.ndarray) -> np.ndarray:
+    """eps of the level-(l-1) cells: the arithmetic mean of their 3^d children
+    (the reading of rediscretisation with a varying parameter; every coarse
+    cell covers the same number of fine cells)."""
+    d = eps.ndim
+    n_c = eps.shape[0] // 3
+    shape = []
+    for _ in range(d):
+        shape += [n_c, 3]
+    return eps.reshape(shape).mean(axis=tuple(range(1, 2 * d, 2)))
+
+
 def build_hierarchy(d: int, L: int, eps, eps_is_scalar: bool, f,
-                    transfer_kind: str = "dlinear") -> Hierarchy:
+                    transfer_kind: str = "dlinear", coarse_op: str = "galerkin") -> Hierarchy:
     """Fine operator from eps, then for l = L .. 2: P_l (d-linear or BoxMG from
-    the level-l stencils), Galerkin A_{l-1} = P_l^T A_l P_l, diagonals."""
+    the level-l stencils), the coarse operator A_{l-1} -- Galerkin
+    P_l^T A_l P_l (Sec. 2.2) or rediscretised from the averaged eps -- and
+    the diagonals."""
     if L < 1:
         raise ValueError("depth must be >= 1")
     n = 3 ** L
@@ -113,7 +127,12 @@ def build_hierarchy(d: int, L: int, eps, eps_is_scalar: bool, f,
             raise ValueError(transfer_kind)
         fine.W = W
         fine.Pv = transfer.vertex_weights(W, n_c)
-        cop = transfer.galerkin(fine.op, W, n_c)
+        if coarse_op == "galerkin":
+            cop = transfer.galerkin(fine.op, W, n_c)
+        elif coarse_op == "rediscretised":
+            cop = LevelOperator.from_eps(d, n_c, coarse_eps(fine.op.eps), False)
+        else:
+            raise ValueError(coarse_op)
         levels[l - 1] = Level(l - 1, n_c, cop, cop.diagonal())
     b = fem.load_vector(f, 1.0 / n, d)
     S_full = smoothed_prolongation_stencil(d)

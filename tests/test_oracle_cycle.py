@@ -291,3 +291,54 @@ def test_boundary_data_match_a_lifted_direct_solve(d, L, transfer_kind):
     assert hist[-1] <= 1e-13
     np.testing.assert_allclose(fem.interior(u).ravel(), x, rtol=1e-9, atol=1e-10)
     np.testing.assert_array_equal(u - fem.zero_boundary(u.copy()), cycle.with_boundary(g))
+
+
+# ---------------------------------------------------------------------------
+# rediscretised coarse operators
+
+def test_rediscretised_levels_are_the_fem_operator_of_the_averaged_eps():
+    d, L = 2, 3
+    rng = np.random.default_rng(9)
+    eps = rng.choice([1.0, 1e-2, 5.0], size=(3 ** L,) * d)
+    H = cycle.build_hierarchy(d, L, eps, False, np.ones((3 ** L + 1,) * d), "boxmg",
+                              coarse_op="rediscretised")
+    e = eps
+    for l in range(L - 1, 0, -1):
+        n_c = 3 ** l
+        avg = np.zeros((n_c,) * d)
+        for i in range(n_c):
+            for j in range(n_c):
+                avg[i, j] = e[3 * i:3 * i + 3, 3 * j:3 * j + 3].sum() / 9.0
+        A = _brute.stiffness_dense(d, n_c, avg)
+        fin = _brute.interior_mask(d, n_c)
+        lv = H.levels[l]
+        Ad = np.stack([fem.interior(lv.op.apply(v.reshape((n_c + 1,) * d))).ravel()
+                       for v in np.eye((n_c + 1) ** d)[fin]], axis=1)
+        np.testing.assert_allclose(Ad, A[np.ix_(fin, fin)], rtol=1e-12, atol=1e-14)
+        e = avg
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rediscretised_equals_galerkin_when_eps_is_constant_on_coarse_cells(d):
+    # d-linear P and eps constant on every level-1 cell: each coarse
+    # rediscretisation is the Galerkin operator (the identity behind Sec. 2.2)
+    L = 3 if d == 2 else 2
+    rng = np.random.default_rng(4)
+    block = rng.choice([1.0, 0.1, 3.0], size=(3,) * d)
+    eps = block
+    for ax in range(d):
+        eps = np.repeat(eps, 3 ** (L - 1), axis=ax)
+    f = np.ones((3 ** L + 1,) * d)
+    Hg = cycle.build_hierarchy(d, L, eps, False, f, "dlinear")
+    Hr = cycle.build_hierarchy(d, L, eps, False, f, "dlinear", coarse_op="rediscretised")
+    for l in range(1, L):
+        n_c = 3 ** l
+        fin = _brute.interior_mask(d, n_c)
+        units = np.eye((n_c + 1) ** d)[fin]
+
+        def dense(op):
+            return np.stack([fem.interior(op.apply(v.reshape((n_c + 1,) * d))).ravel()
+                             for v in units], axis=1)
+
+        np.testing.assert_allclose(dense(Hr.levels[l].op), dense(Hg.levels[l].op),
+                                   rtol=1e-12, atol=1e-13)
