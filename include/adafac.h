@@ -91,12 +91,18 @@ typedef struct {
                          JAC/ADDITIVE/EXP with truncated R~), else one kernel
                          per level and step; ADAFAC_PATH_LEVELWISE: always the
                          latter (same arithmetic, other summation order)      */
+  int coarse_op;      /* ADAFAC_COARSE_GALERKIN (default): A_{l-1} =
+                         P_l^T A_l P_l (Sec. 2.2); ADAFAC_COARSE_REDISCRETISED:
+                         the d-linear FEM operator of level l-1 with the eps of
+                         a coarse cell the mean of its 3^dim children          */
 } adafac_options;
 
 enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1 };
+enum { ADAFAC_COARSE_GALERKIN = 0, ADAFAC_COARSE_REDISCRETISED = 1 };
 
 /* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,
- * inner_cycles 24, omega = omega_tilde = 0.6, omega_exp = 0.5, path AUTO. */
+ * inner_cycles 24, omega = omega_tilde = 0.6, omega_exp = 0.5, path AUTO,
+ * Galerkin coarse operators. */
 adafac_status adafac_default_options(adafac_options* opt);
 
 /* Device bytes a handle for (tree, opt) needs.  Pass at least this much

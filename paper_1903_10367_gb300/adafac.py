@@ -26,6 +26,7 @@ RTILDE = {"truncated": 0, "exact": 1}
 FORM = {"cs": 0, "fas": 1}
 PATH = {"auto": 0, "levelwise": 1}
 FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
+COARSE = {"galerkin": 0, "rediscretised": 1}
 KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,
           "fine_down": 4, "fine_up": 5, "fine_down_u": 6}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DIVERGED", 4: "TIMEOUT", 5: "CUDA",
@@ -56,7 +57,8 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("rtilde", ctypes.c_int),
                 ("form", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double),
-                ("omega_exp", ctypes.c_double), ("path", ctypes.c_int)]
+                ("omega_exp", ctypes.c_double), ("path", ctypes.c_int),
+                ("coarse_op", ctypes.c_int)]
 
 
 _LIB = None
@@ -128,7 +130,7 @@ def default_options(**kw) -> Options:
     _check(lib.adafac_default_options(ctypes.byref(o)))
     for k, v in kw.items():
         table = {"variant": VARIANT, "transfer": TRANSFER, "precision": PRECISION,
-                 "rtilde": RTILDE, "form": FORM, "path": PATH}.get(k)
+                 "rtilde": RTILDE, "form": FORM, "path": PATH, "coarse_op": COARSE}.get(k)
         setattr(o, k, table[v] if table and isinstance(v, str) else v)
     return o
 

@@ -154,6 +154,7 @@ bool valid_options(const adafac_options* o, std::string* why) {
     return *why = "FAS form requires FP64 precision", false;
   if (o->inner_cycles < 1) return *why = "inner_cycles must be >= 1", false;
   if (o->path < 0 || o->path > 1) return *why = "path out of range", false;
+  if (o->coarse_op < 0 || o->coarse_op > 1) return *why = "coarse_op out of range", false;
   if (!(o->omega > 0.0) || !(o->omega_tilde >= 0.0) || !(o->omega_exp > 0.0))
     return *why = "damping factors must be positive", false;
   return true;
@@ -379,7 +380,10 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
       if (check_cuda(h, "boxmg") != ADAFAC_OK) return ADAFAC_ERR_CUDA;
     }
     if (!h->uniform) {
-      launch_galerkin<D>(lf.v64, l == L ? nullptr : lf.Kc, lc.Kc, lc.n, s);
+      if (h->opt.coarse_op == ADAFAC_COARSE_REDISCRETISED)
+        launch_rediscretise<D>(lf.v64, l == L ? nullptr : lf.Kc, lc.Kc, lc.n, s);
+      else
+        launch_galerkin<D>(lf.v64, l == L ? nullptr : lf.Kc, lc.Kc, lc.n, s);
       launch_assemble<D>(lc.Kc, lc.st, lc.invd, lc.n, s);
     } else {
       launch_fine_invdiag<D>(lc.v64, lc.invd, s);
@@ -882,6 +886,7 @@ adafac_status adafac_default_options(adafac_options* o) {
   o->omega_tilde = 0.6;
   o->omega_exp = 0.5;
   o->path = ADAFAC_PATH_AUTO;
+  o->coarse_op = ADAFAC_COARSE_GALERKIN;
   return ADAFAC_OK;
 }
 

@@ -78,6 +78,12 @@ template <int D>
 void launch_fine_invdiag(const LevelView<double>& fine, double* invd, cudaStream_t s);
 template <int D>
 void launch_boxmg(const LevelView<double>& fine, double* P, int n_c, cudaStream_t s);
+// Rediscretised coarse element matrices: eps of a coarse cell = mean of the
+// eps of its 3^D children (from eps on the finest level, from the stored
+// element matrices below it).
+template <int D>
+void launch_rediscretise(const LevelView<double>& fine, const double* Kc_fine, double* Kc,
+                         int n_c, cudaStream_t s);
 template <int D>
 void launch_galerkin(const LevelView<double>& fine, const double* Kc_fine,
                      double* Kc_coarse, int n_c, cudaStream_t s);

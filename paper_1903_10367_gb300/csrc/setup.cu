@@ -397,6 +397,46 @@ __global__ void __launch_bounds__(128) k_galerkin(LevelView<double> fine, const 
   for (int i = 0; i < NC * NC; ++i) Kc[(long long)i * total + E] = K[i];
 }
 
+// Rediscretised element matrices of the coarse level (one thread per coarse
+// cell): eps_E = mean over the 3^D children c of eps_c, K_E = eps_E
+// h_c^(D-2) K_ref.  The children's eps come from the fine eps, or from their
+// stored element matrices (K_c = eps_c h^(D-2) K_ref: entry (0, 0)).
+template <int D>
+__global__ void __launch_bounds__(128) k_rediscretise(LevelView<double> fine,
+                                                      const double* __restrict__ Kc_fine,
+                                                      double* __restrict__ Kc, int n_c) {
+  constexpr int NC = 1 << D;
+  long long total = 1;
+  for (int j = 0; j < D; ++j) total *= n_c;
+  const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (E >= total) return;
+  int ec[D];
+  decode<D>(E, n_c, ec);
+  const int n_f = 3 * n_c;
+  long long ncf = 1;
+  for (int j = 0; j < D; ++j) ncf *= n_f;
+  double sum = 0.0;
+  for (int k = 0; k < ipow_c(3, D); ++k) {
+    int child[D], t = k;
+    for (int j = 0; j < D; ++j) {
+      child[j] = 3 * ec[j] + t % 3;
+      t /= 3;
+    }
+    const long long c = encode<D>(child, n_f);
+    double e;
+    if (Kc_fine)
+      e = Kc_fine[c] / (fine.hfac * kref<D, double>(0));
+    else
+      e = fine.opkind == OP_EPS ? fine.eps[c] : fine.eps0;
+    sum += e;
+  }
+  const double eps = sum / (double)ipow_c(3, D);
+  const double hfac = D == 2 ? 1.0 : 1.0 / n_c;
+  for (int a = 0; a < NC; ++a)
+    for (int b = 0; b < NC; ++b)
+      Kc[(long long)(a * NC + b) * total + E] = eps * hfac * kref<D, double>(__popc(a ^ b));
+}
+
 // Assembled 3^D stencil and inverse diagonal of every vertex from the
 // per-cell element matrices (entry-major layouts).
 template <int D>
@@ -483,6 +523,14 @@ void launch_galerkin(const LevelView<double>& fine, const double* Kc_fine, doubl
 }
 
 template <int D>
+void launch_rediscretise(const LevelView<double>& fine, const double* Kc_fine, double* Kc,
+                         int n_c, cudaStream_t s) {
+  long long total = 1;
+  for (int j = 0; j < D; ++j) total *= n_c;
+  k_rediscretise<D><<<blocks_for(total, 128), 128, 0, s>>>(fine, Kc_fine, Kc, n_c);
+}
+
+template <int D>
 void launch_assemble(const double* Kc, double* st, double* invd, int n, cudaStream_t s) {
   long long V = 1;
   for (int j = 0; j < D; ++j) V *= n + 1;
@@ -503,7 +551,9 @@ void launch_fill(double* dst, double value, long long count, cudaStream_t s) {
   template void launch_boxmg<D>(const LevelView<double>&, double*, int, cudaStream_t);       \
   template void launch_galerkin<D>(const LevelView<double>&, const double*, double*, int,    \
                                    cudaStream_t);                                            \
-  template void launch_assemble<D>(const double*, double*, double*, int, cudaStream_t);
+  template void launch_assemble<D>(const double*, double*, double*, int, cudaStream_t);    \
+  template void launch_rediscretise<D>(const LevelView<double>&, const double*, double*, int, \
+                                       cudaStream_t);
 
 ADAFAC_SETUP_INST(2)
 ADAFAC_SETUP_INST(3)

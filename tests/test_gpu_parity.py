@@ -41,7 +41,7 @@ def _case(d, L, eps_kind="scalar", transfer="dlinear", seed=5, rhs="manufactured
 
 def _pair(d, L, eps_kind="scalar", transfer="dlinear", **opt):
     eps, sc, f = _case(d, L, eps_kind, transfer)
-    H = oc.build_hierarchy(d, L, eps, sc, f, transfer)
+    H = oc.build_hierarchy(d, L, eps, sc, f, transfer, coarse_op=opt.get("coarse_op", "galerkin"))
     o = adafac.default_options(transfer=transfer, **opt)
     S = adafac.Solver(d, L, float(eps[0]) if sc else eps, f, o)
     return H, S
@@ -75,6 +75,23 @@ def test_boxmg_and_galerkin_setup_match_oracle(d, L, eps_kind):
     S.close()
 
 
+@pytest.mark.parametrize("d,L,eps_kind,transfer", [(2, 4, "blocks", "boxmg"), (3, 3, "random", "dlinear")])
+def test_rediscretised_coarse_operators_match_oracle(d, L, eps_kind, transfer):
+    H, S = _pair(d, L, eps_kind, transfer, coarse_op="rediscretised")
+    I = tuple(slice(1, -1) for _ in range(d))
+    for l in range(1, L):
+        st = S.field("stencil", l)
+        want = H.levels[l].op.stencils()
+        # relative to the largest entry: the face entries of the 3-D d-linear
+        # element are zero (the oracle's carry rounding noise)
+        scale = np.abs(want[I]).max()
+        for s in range(3 ** d):
+            err = np.abs(st[s][I] - want[..., s][I]).max() / scale
+            assert err <= 1e-12, f"stencil level {l} entry {s}: {err:.3e}"
+        _close(S.field("invdiag", l)[I], 1.0 / H.levels[l].diag[I], 1e-12, f"invdiag level {l}")
+    S.close()
+
+
 def test_uniform_levels_match_galerkin_for_constant_eps():
     # scalar eps with d-linear transfers keeps every level's stencil uniform;
     # the oracle forms R A P explicitly
@@ -105,6 +122,9 @@ CASES = [
     (3, 3, "random", "boxmg", dict(variant="jac")),
     (3, 3, "random", "dlinear", dict(variant="pi", form="fas")),
     (3, 2, "random", "boxmg", dict(variant="jac", rtilde="exact")),
+    (2, 4, "blocks", "boxmg", dict(variant="jac", coarse_op="rediscretised")),
+    (2, 3, "random", "dlinear", dict(variant="pi", coarse_op="rediscretised")),
+    (3, 3, "random", "boxmg", dict(variant="jac", coarse_op="rediscretised")),
 ]
 
 
