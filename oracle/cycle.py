@@ -253,34 +253,39 @@ def level_residuals(H: Hierarchy, u: np.ndarray, form: str):
 def cycle(H: Hierarchy, u: np.ndarray, variant: str = "jac", form: str = "cs",
           rtilde: str = "truncated", omega: float = OMEGA,
           omega_tilde: float = OMEGA_TILDE, omega_exp: float = 0.5,
-          return_parts: bool = False):
-    """One additive cycle; returns the new fine iterate (and the level data).
+          return_parts: bool = False, lmin: int = 1):
+    """One additive cycle over the levels lmin .. L; returns the new fine
+    iterate (and the level data).
 
     Reading of Alg. 1's final update (its printed sum starts one level too
-    coarse and counts c_{l_min} twice): u += sum_{l=1}^{L} P^{L-l} c_l
-    - sum_{l=2}^{L} P^{L-l+1} c~_{l-1}, which is Eq. 9 with M^{-1}_{l_min-1}
-    = 0 (no damping on the coarsest level).  Alg. 2 is read the same way."""
+    coarse and counts c_{l_min} twice): u += sum_{l=lmin}^{L} P^{L-l} c_l
+    - sum_{l=lmin+1}^{L} P^{L-l+1} c~_{l-1}, which is Eq. 9 with
+    M^{-1}_{l_min-1} = 0 (no damping below the coarsest level).  Alg. 2 is read
+    the same way.  lmin > 1 drops the coarser levels (Sec. 5 adds correction
+    levels one by one below a fixed finest level)."""
     L = H.L
+    if not 1 <= lmin <= L:
+        raise ValueError("lmin must be in 1 .. L")
     r = level_residuals(H, u, form)
-    c = {l: jacobi_correction(H, l, r[l], omega) for l in range(1, L + 1)}
+    c = {l: jacobi_correction(H, l, r[l], omega) for l in range(lmin, L + 1)}
     du = np.zeros_like(u)
     parts = {"r": r, "c": c}
     if variant in ("jac", "additive", "exp"):
-        for l in range(1, L + 1):
+        for l in range(lmin, L + 1):
             scale = omega_exp ** (L - l) if variant == "exp" else 1.0
             du += scale * P_pow(H, l, L, c[l])
     if variant == "jac":
         bt, ct = {}, {}
-        for l in range(2, L + 1):
+        for l in range(lmin + 1, L + 1):
             bt[l - 1] = Rtilde(H, l, r[l], omega, rtilde)
             ct[l - 1] = jacobi_correction(H, l - 1, bt[l - 1], omega_tilde)
             du -= P_pow(H, l - 1, L, ct[l - 1])
         parts["bt"], parts["ct"] = bt, ct
     elif variant == "pi":
         ct = {}
-        for l in range(1, L + 1):
+        for l in range(lmin, L + 1):
             du += P_pow(H, l, L, c[l])
-        for l in range(2, L + 1):
+        for l in range(lmin + 1, L + 1):
             ct[l] = P(H, l, zero_boundary(transfer.inject(c[l])))
             du -= P_pow(H, l, L, ct[l])
         parts["ct"] = ct

@@ -122,18 +122,20 @@ def _rtilde_truncated_2d_dense(n_c):
     return Rt
 
 
-@pytest.mark.parametrize("d,L,variant,rtilde", [
-    (2, 2, "jac", "truncated"), (2, 3, "jac", "truncated"), (2, 3, "jac", "exact"),
-    (2, 3, "additive", "truncated"), (2, 3, "pi", "truncated"), (2, 3, "exp", "truncated"),
-    (3, 2, "jac", "exact"), (3, 2, "pi", "exact")])
-def test_cycle_equals_dense_restatement_of_eq9(d, L, variant, rtilde):
+@pytest.mark.parametrize("d,L,variant,rtilde,lmin", [
+    (2, 2, "jac", "truncated", 1), (2, 3, "jac", "truncated", 1), (2, 3, "jac", "exact", 1),
+    (2, 3, "additive", "truncated", 1), (2, 3, "pi", "truncated", 1),
+    (2, 3, "exp", "truncated", 1), (3, 2, "jac", "exact", 1), (3, 2, "pi", "exact", 1),
+    (2, 3, "jac", "truncated", 2), (2, 3, "pi", "truncated", 2), (2, 3, "jac", "exact", 3)])
+def test_cycle_equals_dense_restatement_of_eq9(d, L, variant, rtilde, lmin):
     rng = np.random.default_rng(12)
     n = 3 ** L
     eps = rng.uniform(0.2, 3.0, size=(n,) * d)
     f = rng.standard_normal((n + 1,) * d)
     H = cycle.build_hierarchy(d, L, eps, False, f)
     u = fem.zero_boundary(rng.standard_normal((n + 1,) * d))
-    got = fem.interior(cycle.cycle(H, u, variant=variant, rtilde=rtilde, omega_exp=0.7)).ravel()
+    got = fem.interior(cycle.cycle(H, u, variant=variant, rtilde=rtilde, omega_exp=0.7,
+                                   lmin=lmin)).ravel()
 
     A, Pm, D = _dense_hierarchy(d, L, eps)
     w = wt = 0.6
@@ -148,18 +150,18 @@ def test_cycle_equals_dense_restatement_of_eq9(d, L, variant, rtilde):
         return M
 
     M = np.zeros((A[L].shape[0], A[L].shape[0]))
-    for l in range(1, L + 1):
+    for l in range(lmin, L + 1):
         scale = 0.7 ** (L - l) if variant == "exp" else 1.0
         M += scale * Pchain(l) @ (w * np.linalg.inv(D[l])) @ Pchain(l).T
     if variant == "jac":
-        for l in range(2, L + 1):
+        for l in range(lmin + 1, L + 1):
             if rtilde == "exact":
                 Rt = w * Pm[l].T @ A[l] @ np.linalg.inv(D[l])
             else:
                 Rt = w * _rtilde_truncated_2d_dense(3 ** (l - 1))
             M -= Pchain(l - 1) @ (wt * np.linalg.inv(D[l - 1])) @ Rt @ Pchain(l).T
     if variant == "pi":
-        for l in range(2, L + 1):
+        for l in range(lmin + 1, L + 1):
             PI = Pm[l] @ _injection_dense(d, 3 ** (l - 1))
             M -= Pchain(l) @ PI @ (w * np.linalg.inv(D[l])) @ Pchain(l).T
     want = ui + M @ r
