@@ -95,6 +95,9 @@ typedef struct {
                          P_l^T A_l P_l (Sec. 2.2); ADAFAC_COARSE_REDISCRETISED:
                          the d-linear FEM operator of level l-1 with the eps of
                          a coarse cell the mean of its 3^dim children          */
+  int lmin;           /* coarsest level taking part in the cycles, 1 (default)
+                         .. depth; levels below lmin are not used (Sec. 5 adds
+                         correction levels one by one below the finest)      */
 } adafac_options;
 
 enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1 };
@@ -102,7 +105,7 @@ enum { ADAFAC_COARSE_GALERKIN = 0, ADAFAC_COARSE_REDISCRETISED = 1 };
 
 /* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,
  * inner_cycles 24, omega = omega_tilde = 0.6, omega_exp = 0.5, path AUTO,
- * Galerkin coarse operators. */
+ * Galerkin coarse operators, lmin 1. */
 adafac_status adafac_default_options(adafac_options* opt);
 
 /* Device bytes a handle for (tree, opt) needs.  Pass at least this much

@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
                 ("form", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("omega", ctypes.c_double), ("omega_tilde", ctypes.c_double),
                 ("omega_exp", ctypes.c_double), ("path", ctypes.c_int),
-                ("coarse_op", ctypes.c_int)]
+                ("coarse_op", ctypes.c_int), ("lmin", ctypes.c_int)]
 
 
 _LIB = None

@@ -155,6 +155,7 @@ bool valid_options(const adafac_options* o, std::string* why) {
   if (o->inner_cycles < 1) return *why = "inner_cycles must be >= 1", false;
   if (o->path < 0 || o->path > 1) return *why = "path out of range", false;
   if (o->coarse_op < 0 || o->coarse_op > 1) return *why = "coarse_op out of range", false;
+  if (o->lmin < 1) return *why = "lmin must be >= 1", false;
   if (!(o->omega > 0.0) || !(o->omega_tilde >= 0.0) || !(o->omega_exp > 0.0))
     return *why = "damping factors must be positive", false;
   return true;
@@ -174,7 +175,7 @@ bool valid_tree(const adafac_tree* t, std::string* why) {
 // of plain / exponentially damped additive multigrid, in correction form.
 bool fast3_eligible(const adafac_handle_s* h) {
   const adafac_options& o = h->opt;
-  return o.path == ADAFAC_PATH_AUTO && h->D == 3 && h->L >= 2 && h->uniform &&
+  return o.path == ADAFAC_PATH_AUTO && h->D == 3 && h->L >= 2 && o.lmin < h->L && h->uniform &&
          o.precision == ADAFAC_PRECISION_MIXED &&
          o.form == ADAFAC_FORM_CS && o.rtilde == ADAFAC_RTILDE_TRUNCATED &&
          (o.variant == ADAFAC_VARIANT_JAC || o.variant == ADAFAC_VARIANT_ADDITIVE ||
@@ -538,6 +539,7 @@ double hD_of(adafac_handle h) {
 template <int D>
 void fp64_cycle(adafac_handle h) {
   const int L = h->L;
+  const int lmin = h->opt.lmin;
   cudaStream_t s = h->stream;
   LevelData* lv = h->lev;
   const CycleParams<double>& cp = h->cp64;
@@ -552,7 +554,7 @@ void fp64_cycle(adafac_handle h) {
   if (fas) {
     // Eq. 4: u_l = I u_{l+1}, u^_{l+1} = u_{l+1} - P u_l,
     // b_l = R (b_{l+1} - A_{l+1} u^_{l+1}), r_l = b_l - A_l u_l
-    for (int l = L - 1; l >= 1; --l) {
+    for (int l = L - 1; l >= lmin; --l) {
       const double* uf = l + 1 == L ? h->u : lv[l + 1].ul;
       const double* bf = l + 1 == L ? h->b : lv[l + 1].bl;
       launch_inject<D>(uf, lv[l + 1].n, lv[l].ul, h->ctl, s);
@@ -565,7 +567,7 @@ void fp64_cycle(adafac_handle h) {
       h->launches += 5;
     }
   }
-  for (int l = L - 1; l >= 1; --l) {
+  for (int l = L - 1; l >= lmin; --l) {
     const double gscale =
         cp.variant == V_EXP ? std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0;
     if (exact) {
@@ -579,15 +581,15 @@ void fp64_cycle(adafac_handle h) {
     h->launches += 1;
   }
   // t_1 = g_1; t_l = g_l + P q_{l-1}
-  for (int l = 2; l <= L - 1; ++l) {
-    const double* tc = l - 1 == 1 ? lv[1].g : lv[l - 1].t;
+  for (int l = lmin + 1; l <= L - 1; ++l) {
+    const double* tc = l - 1 == lmin ? lv[lmin].g : lv[l - 1].t;
     launch_prolong<D, double>(lv[l].v64, lv[l - 1].v64, cp, tc, lv[l].g, lv[l].t, h->ctl, s);
     h->launches += 1;
   }
   LevelView<double> empty;
-  const double* tc = L >= 2 ? (L - 1 == 1 ? lv[1].g : lv[L - 1].t) : nullptr;
+  const double* tc = L > lmin ? (L - 1 == lmin ? lv[lmin].g : lv[L - 1].t) : nullptr;
   timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] {
-    launch_update<D, double, double>(lv[L].v64, L >= 2 ? lv[L - 1].v64 : empty, cp, lv[L].r,
+    launch_update<D, double, double>(lv[L].v64, L > lmin ? lv[L - 1].v64 : empty, cp, lv[L].r,
                                      tc, h->u, h->ctl, s);
   });
   h->launches += 1;
@@ -597,6 +599,7 @@ void fp64_cycle(adafac_handle h) {
 template <int D>
 void fp32_cycle(adafac_handle h) {
   const int L = h->L;
+  const int lmin = h->opt.lmin;
   cudaStream_t s = h->stream;
   LevelData* lv = h->lev;
   const CycleParams<float>& cp = h->cp32;
@@ -606,7 +609,7 @@ void fp32_cycle(adafac_handle h) {
                                      0, 0.0, h->ctl, s);
   });
   h->launches += 1;
-  for (int l = L - 1; l >= 1; --l) {
+  for (int l = L - 1; l >= lmin; --l) {
     const float gscale =
         cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
     if (exact) {
@@ -619,15 +622,15 @@ void fp32_cycle(adafac_handle h) {
     });
     h->launches += 1;
   }
-  for (int l = 2; l <= L - 1; ++l) {
-    const float* tc = l - 1 == 1 ? lv[1].g32 : lv[l - 1].t32;
+  for (int l = lmin + 1; l <= L - 1; ++l) {
+    const float* tc = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
     launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
     h->launches += 1;
   }
   LevelView<float> empty;
-  const float* tc = L >= 2 ? (L - 1 == 1 ? lv[1].g32 : lv[L - 1].t32) : nullptr;
+  const float* tc = L > lmin ? (L - 1 == lmin ? lv[lmin].g32 : lv[L - 1].t32) : nullptr;
   timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] {
-    launch_update<D, float, float>(lv[L].v32, L >= 2 ? lv[L - 1].v32 : empty, cp, lv[L].r32,
+    launch_update<D, float, float>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, cp, lv[L].r32,
                                    tc, h->e32, h->ctl, s);
   });
   h->launches += 1;
@@ -659,18 +662,19 @@ void mixed_step(adafac_handle h, int k) {
 template <int D>
 void coarse_chain32(adafac_handle h) {
   const int L = h->L;
+  const int lmin = h->opt.lmin;
   cudaStream_t s = h->stream;
   LevelData* lv = h->lev;
   const CycleParams<float>& cp = h->cp32;
-  for (int l = L - 2; l >= 1; --l) {
+  for (int l = L - 2; l >= lmin; --l) {
     const float gscale =
         cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
     launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
                               lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
     h->launches += 1;
   }
-  for (int l = 2; l <= L - 1; ++l) {
-    const float* tc = l - 1 == 1 ? lv[1].g32 : lv[l - 1].t32;
+  for (int l = lmin + 1; l <= L - 1; ++l) {
+    const float* tc = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
     launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
     h->launches += 1;
   }
@@ -694,7 +698,8 @@ int fast3_step(adafac_handle h, int k, int ebase) {
                        kHistCap, 0, s);
   h->launches += 3;
   Sweep3Params p = h->sw;
-  p.q = L - 1 == 1 ? h->lev[1].g32 : h->lev[L - 1].t32;
+  const int lmin = h->opt.lmin;
+  p.q = L - 1 == lmin ? h->lev[lmin].g32 : h->lev[L - 1].t32;
   float* E[2] = {h->e32, h->e32b};
   int cur = ebase;
   timed(h, ADAFAC_KERNEL_FINE_RESTRICT,
@@ -887,6 +892,7 @@ adafac_status adafac_default_options(adafac_options* o) {
   o->omega_exp = 0.5;
   o->path = ADAFAC_PATH_AUTO;
   o->coarse_op = ADAFAC_COARSE_GALERKIN;
+  o->lmin = 1;
   return ADAFAC_OK;
 }
 
@@ -896,7 +902,6 @@ adafac_status adafac_workspace_size(const adafac_tree* tree, const adafac_option
   if (!tree || !opt || !bytes) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null argument");
   if (!valid_tree(tree, &why) || !valid_options(opt, &why))
     return fail(nullptr, ADAFAC_ERR_INVALID_ARG, why);
-  // The size depends on whether eps is scalar; report the larger (per-cell) case.
   // the size depends on whether eps is scalar: report the larger of both
   size_t most = 0;
   for (int scalar = 0; scalar <= 1; ++scalar) {
@@ -932,6 +937,8 @@ adafac_status adafac_setup(const adafac_tree* tree, const double* eps, int eps_i
   if (!tree || !opt || !eps) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null argument");
   if (!valid_tree(tree, &why) || !valid_options(opt, &why))
     return fail(nullptr, ADAFAC_ERR_INVALID_ARG, why);
+  if (opt->lmin > tree->depth)
+    return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "lmin must not exceed the depth");
   adafac_handle h = new (std::nothrow) adafac_handle_s();
   if (!h) return fail(nullptr, ADAFAC_ERR_OOM, "host allocation failed");
   h->D = tree->dim;
@@ -1159,8 +1166,8 @@ adafac_status adafac_get_field(adafac_handle h, int field, int level, double* ds
       break;
     case ADAFAC_FIELD_T:
       if (level == h->L) return fail(h, ADAFAC_ERR_INVALID_ARG, "T lives on levels < L");
-      if (mixed) src32 = level == 1 ? lv.g32 : lv.t32;
-      else src64 = level == 1 ? lv.g : lv.t;
+      if (mixed) src32 = level == h->opt.lmin ? lv.g32 : lv.t32;
+      else src64 = level == h->opt.lmin ? lv.g : lv.t;
       break;
     case ADAFAC_FIELD_P:
       if (!lv.P) return fail(h, ADAFAC_ERR_INVALID_ARG, "P is stored for BoxMG levels >= 2 only");

@@ -173,3 +173,20 @@ def test_maximum_size_poisson3d_d6_mixed_fused():
     err5 = np.abs(S5.solution() - wl.manufactured_solution(3, 5)).max()
     S5.close()
     assert 8.0 < err5 / err6 < 10.0
+
+
+@pytest.mark.parametrize("L,lmin", [(4, 2), (4, 3), (3, 2)])
+def test_fused_with_fewer_levels_equals_levelwise_and_oracle(L, lmin):
+    a = _solver(L, "auto", inner_cycles=3, lmin=lmin)
+    b = _solver(L, "levelwise", inner_cycles=3, lmin=lmin)
+    a.cycle(7)
+    b.cycle(7)
+    ua, ub = a.solution(), b.solution()
+    assert _rel(ua, ub) < FP32_RTOL
+    H = oc.build_hierarchy(3, L, [1.0], True, wl.manufactured_rhs(3, L))
+    u = np.zeros_like(H.b)
+    for _ in range(7):
+        u = oc.cycle(H, u, lmin=lmin)
+    assert _rel(ua, u) < FP32_RTOL
+    a.close()
+    b.close()

@@ -125,11 +125,15 @@ CASES = [
     (2, 4, "blocks", "boxmg", dict(variant="jac", coarse_op="rediscretised")),
     (2, 3, "random", "dlinear", dict(variant="pi", coarse_op="rediscretised")),
     (3, 3, "random", "boxmg", dict(variant="jac", coarse_op="rediscretised")),
+    (2, 4, "blocks", "boxmg", dict(variant="jac", lmin=2)),
+    (2, 4, "scalar", "dlinear", dict(variant="pi", lmin=3)),
+    (2, 4, "scalar", "dlinear", dict(variant="additive", lmin=4)),
+    (3, 3, "random", "dlinear", dict(variant="jac", lmin=2)),
 ]
 
 
 def _oracle_kw(opt):
-    return dict(variant=opt.get("variant", "jac"), form=opt.get("form", "cs"),
+    return dict(lmin=opt.get("lmin", 1), variant=opt.get("variant", "jac"), form=opt.get("form", "cs"),
                 rtilde=opt.get("rtilde", "truncated"), omega_exp=opt.get("omega_exp", 0.5))
 
 
@@ -141,10 +145,11 @@ def test_one_cycle_matches_oracle(d, L, eps_kind, transfer, opt):
     S.cycle(1)
     u1, parts = oc.cycle(H, u0, return_parts=True, **_oracle_kw(opt))
     _close(S.solution(), u1, RTOL, "u after one cycle")
-    for l in range(1, L + 1):
+    lmin = opt.get("lmin", 1)
+    for l in range(lmin, L + 1):
         _close(S.field("r", l), parts["r"][l], RTOL, f"r level {l}")
     if opt.get("variant", "jac") == "jac":
-        for l in range(1, L):
+        for l in range(lmin, L):
             _close(S.field("bt", l), parts["bt"][l], RTOL, f"b~ level {l}")
             want_g = parts["c"][l] - parts["ct"][l]
             _close(S.field("g", l), want_g, RTOL, f"g level {l}")
