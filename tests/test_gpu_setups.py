@@ -131,3 +131,41 @@ def test_stability_on_regular_trees_halves_jump():
     for variant in ("additive", "jac", "pi"):
         c = run("boxmg", variant)
         assert c is not None and c < c_jac
+
+
+def test_oscillations_grow_with_the_number_of_correction_levels():
+    # Sec. 5, regular level 6, eps jump of seven orders across x_1 = 1/2: the
+    # sample point next to (1/2, 1/2), normalised by the converged value,
+    # oscillates when correction levels are added below the finest (l_min
+    # lowered) with d-linear transfers and plain additive multigrid; the
+    # additive damping of adAFAC-Jac shrinks the oscillations by orders of
+    # magnitude, and BoxMG transfers remove them
+    L = 6
+    n = 3 ** L
+    eps = wl.eps_halves(2, L, 1e-7)
+    g = wl.bottom_boundary(2, L)
+    f = np.zeros((n + 1,) * 2)
+    sy, sx = n // 2, n // 2 + 1
+    S = adafac.Solver(2, L, eps, f, adafac.default_options(transfer="boxmg"))
+    S.set_boundary(g)
+    S.solve(1e-12, 20000)
+    ref = S.solution()[sy, sx]
+    S.close()
+
+    def amplitude(transfer, variant, lmin, cycles=80):
+        S = adafac.Solver(2, L, eps, f, adafac.default_options(transfer=transfer,
+                                                               variant=variant, lmin=lmin))
+        S.set_boundary(g)
+        t = []
+        for _ in range(cycles):
+            S.cycle(1)
+            t.append(S.solution()[sy, sx] / ref)
+        S.close()
+        t = np.array(t)
+        return max(t.max() - 1.0, 0.0) + max(-t.min(), 0.0)
+
+    add = {lmin: amplitude("dlinear", "additive", lmin) for lmin in (3, 2, 1)}
+    assert add[3] < 0.01 < add[2] < add[1]
+    assert add[1] > 1000.0
+    assert amplitude("dlinear", "jac", 1) < 1e-2 * add[1]
+    assert amplitude("boxmg", "additive", 1) < 0.1
