@@ -479,7 +479,16 @@ __global__ void __launch_bounds__(UNT, 3)
   float2 PR[URC], YR[URC];
 #pragma unroll
   for (int i = 0; i < URC; ++i) PR[i] = YR[i] = f2(0.f);
-  float accR[2] = {0.f, 0.f}, accB[2] = {0.f, 0.f};
+  // restriction and damping sums of the coarse plane being completed (cur)
+  // and of the next one (nxt); the class weights of S~ by |oz| in registers
+  float curR = 0.f, curB = 0.f, nxtR = 0.f, nxtB = 0.f;
+  float dz0[6], dz1[6], dz2[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    dz0[k] = p.dcls[k];
+    dz1[k] = p.dcls[6 + k];
+    dz2[k] = p.dcls[12 + k];
+  }
   // restriction geometry: coarse column tid
   const bool hasJ = tid < UNJ;
   const int cjx = tid % UBJX, cjy = tid / UBJX;
@@ -569,38 +578,44 @@ __global__ void __launch_bounds__(UNT, 3)
       }
       const float rin = c0 + (2.f / 3.f) * l1 + (1.f / 3.f) * l2 + (4.f / 9.f) * p11 +
                         (2.f / 9.f) * p12 + (1.f / 9.f) * p22;
-      const int jtop = (r + 2) / 3;  // r >= -2
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const int Jz = jtop - 1 + d;
-        const int oz = r - 3 * Jz;
-        if (oz < -2 || oz > 2 || Jz < Jz0 || Jz >= Jz1) continue;
-        const int az = oz < 0 ? -oz : oz;
-        const int slot = Jz & 1;
-        float aR = slot ? accR[1] : accR[0];
-        float aB = slot ? accB[1] : accB[0];
-        if (oz == -2) aR = aB = 0.f;
-        aR = fmaf(1.f - (float)az * (1.f / 3.f), rin, aR);
-        const float* dz = p.dcls + 6 * az;
-        aB += dz[0] * c0 + dz[1] * l1 + dz[2] * l2 + dz[3] * p11 + dz[4] * p12 + dz[5] * p22;
-        if (slot) {
-          accR[1] = aR;
-          accB[1] = aB;
+      // fine plane r = 3 m + ph lies at oz = ph from coarse plane m and at
+      // oz = ph - 3 from m + 1: ph 0 adds to m only; ph 1 adds oz = 1 to m and
+      // opens m + 1 with oz = -2; ph 2 completes m (oz = 2) and adds oz = -1 to
+      // m + 1.  The phase is the same for the whole block, so the branches do
+      // not diverge and the weights of |oz| are compile-time indices.
+      const int ph = (r + 3) % 3;  // r >= -2
+      const int m = (r + 3) / 3 - 1;
+      if (ph == 0) {
+        curR += rin;
+        curB += dz0[0] * c0 + dz0[1] * l1 + dz0[2] * l2 + dz0[3] * p11 + dz0[4] * p12 +
+                dz0[5] * p22;
+      } else {
+        const float b1 = dz1[0] * c0 + dz1[1] * l1 + dz1[2] * l2 + dz1[3] * p11 +
+                         dz1[4] * p12 + dz1[5] * p22;
+        const float b2 = dz2[0] * c0 + dz2[1] * l1 + dz2[2] * l2 + dz2[3] * p11 +
+                         dz2[4] * p12 + dz2[5] * p22;
+        if (ph == 1) {
+          curR = fmaf(2.f / 3.f, rin, curR);
+          curB += b1;
+          nxtR = (1.f / 3.f) * rin;
+          nxtB = b2;
         } else {
-          accR[0] = aR;
-          accB[0] = aB;
-        }
-        if (oz == 2 && outJ && Jz >= 1 && Jz <= nc - 1) {
-          const float bt = p.omega * aB;
-          const long long ci = ((long long)Jz * ncp1 + Jy) * ncp1 + Jx;
-          p.r_c[ci] = aR;
-          if (p.variant == V_JAC) {
-            p.bt_c[ci] = bt;
-            p.g_c[ci] = p.c_invd * (p.omega * aR - p.omega_t * bt);
-          } else {
-            p.bt_c[ci] = 0.f;
-            p.g_c[ci] = p.gscale * p.omega * p.c_invd * aR;
+          const float aR = fmaf(1.f / 3.f, rin, curR);
+          const float aB = curB + b2;
+          if (outJ && m >= Jz0 && m >= 1 && m <= nc - 1) {
+            const float bt = p.omega * aB;
+            const long long ci = ((long long)m * ncp1 + Jy) * ncp1 + Jx;
+            p.r_c[ci] = aR;
+            if (p.variant == V_JAC) {
+              p.bt_c[ci] = bt;
+              p.g_c[ci] = p.c_invd * (p.omega * aR - p.omega_t * bt);
+            } else {
+              p.bt_c[ci] = 0.f;
+              p.g_c[ci] = p.gscale * p.omega * p.c_invd * aR;
+            }
           }
+          curR = fmaf(2.f / 3.f, rin, nxtR);
+          curB = nxtB + b1;
         }
       }
     }
