@@ -100,6 +100,9 @@ struct adafac_handle_s {
   Sweep3Maps maps;
   Sweep3Params sw;
   Refine3Params rf;
+  Coarse3Params c3;          // levels lmin .. min(L - 1, 3) in one launch
+  size_t c3_bytes = 0;
+  bool c3_ok = false;
   // CUDA graphs of whole cycle batches / refinement steps
   bool use_graphs = true;
   cudaStream_t cap = nullptr;
@@ -467,6 +470,31 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw.omega_t = (float)h->opt.omega_tilde;
     sw.gscale = h->opt.variant == ADAFAC_VARIANT_EXP ? (float)h->opt.omega_exp : 1.0f;
     sw.variant = h->opt.variant;
+    // the small coarse levels in one launch
+    Coarse3Params& c3 = h->c3;
+    c3 = Coarse3Params();
+    c3.T = std::min(L - 1, kCoarse3Top);
+    c3.lmin = h->opt.lmin;
+    c3.variant = h->opt.variant;
+    c3.omega = (float)h->opt.omega;
+    c3.omega_t = (float)h->opt.omega_tilde;
+    for (int l = 1; l <= c3.T; ++l) {
+      c3.gscale[l] = h->opt.variant == ADAFAC_VARIANT_EXP
+                         ? (float)std::pow(h->opt.omega_exp, (double)(L - l))
+                         : 1.0f;
+      c3.r[l] = h->lev[l].r32;
+      c3.bt[l] = h->lev[l].bt32;
+      c3.g[l] = h->lev[l].g32;
+      c3.t[l] = h->lev[l].t32;
+      c3.invd[l] = h->lev[l].invd32;
+    }
+    for (int k = 0; k < 125; ++k) c3.stilde[k] = (float)sd[k];
+    c3.ctl = h->ctl;
+    c3.fault = &h->ctl->fault;
+    c3.fault_info = &h->ctl->fault_info[0];
+    coarse3_layout(&c3, &h->c3_bytes);
+    h->c3_ok = c3.T > c3.lmin && coarse3_prepare();
+    cudaGetLastError();
     // S~ by class (|oz|; in-plane distances); the class form is exact because
     // S~ is symmetric under reflections and permutations of the axes -- checked
     const int cls_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
@@ -666,14 +694,21 @@ void coarse_chain32(adafac_handle h) {
   cudaStream_t s = h->stream;
   LevelData* lv = h->lev;
   const CycleParams<float>& cp = h->cp32;
-  for (int l = L - 2; l >= lmin; --l) {
+  // levels lmin .. T run in one launch when the fused kernel is available
+  const int T = h->c3_ok ? h->c3.T : lmin;
+  const int top = std::max(lmin, T);
+  for (int l = L - 2; l >= top; --l) {
     const float gscale =
         cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
     launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
                               lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
     h->launches += 1;
   }
-  for (int l = lmin + 1; l <= L - 1; ++l) {
+  if (T > lmin) {
+    launch_coarse3(h->c3, h->c3_bytes, s);
+    h->launches += 1;
+  }
+  for (int l = top + 1; l <= L - 1; ++l) {
     const float* tc = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
     launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
     h->launches += 1;

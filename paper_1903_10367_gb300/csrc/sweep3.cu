@@ -35,6 +35,7 @@
 //     restriction and the damping right-hand side of their coarse columns as
 //     the planes pass.
 #include "common.cuh"
+#include "mbarrier.cuh"
 #include "sweep3.cuh"
 
 namespace adafac {
@@ -52,8 +53,6 @@ constexpr int NSTAGE = 3, PREF = 2;         // ring slots, planes staged ahead
 constexpr int QW = 24, QH = BJY + 4;        // coarse q window
 constexpr int NQX = QH * 64;                // x-interpolated coarse values per plane
 
-constexpr long kWaitLimit = 1L << 22;       // polls before a wait gives up
-constexpr unsigned long long kWaitNs = 2000000000ull;  // or device time (2 s)
 static_assert(BOXW * BOXH <= PLANE_F, "staged box fits its slot");
 static_assert((BOXW * 4) % 16 == 0, "box rows are 16-byte multiples");
 static_assert(BOXW >= 68 && BOXH >= OH + 6, "the box covers 64 columns and the rows + halo");
@@ -77,48 +76,6 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// bounded wait on a phase of an mbarrier: gives up after kWaitNs of device
-// time or kWaitLimit polls, whichever comes first
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (long i = 0; i < kWaitLimit; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
 
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* tm, int x, int y, int z,
                                          uint32_t bar) {
@@ -206,7 +163,7 @@ __global__ void __launch_bounds__(NT, MINB)
   if (tid == 0) {
     s_fail = 0;
     for (int k = 0; k < NSTAGE; ++k) mbar_init(bar0 + 8 * k);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   __syncthreads();
   if (tid == 0)
@@ -454,7 +411,7 @@ __global__ void __launch_bounds__(UNT, 3)
   if (tid == 0) {
     s_fail = 0;
     for (int k = 0; k < NSTAGE; ++k) mbar_init(bar0 + 8 * k);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   __syncthreads();
   if (tid == 0)
