@@ -373,7 +373,7 @@ def kernel_source_hash():
     import hashlib
     csrc = os.path.join(ROOT, "paper_1903_10367_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("sweep3.cu", "sweep3.cuh", "common.cuh"):
+    for name in ("sweep3.cu", "sweep3.cuh", "common.cuh", "mbarrier.cuh"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
