@@ -100,9 +100,6 @@ struct adafac_handle_s {
   Sweep3Maps maps;
   Sweep3Params sw;
   Refine3Params rf;
-  Coarse3Params c3;          // levels lmin .. min(L - 1, 3) in one launch
-  size_t c3_bytes = 0;
-  bool c3_ok = false;
   // CUDA graphs of whole cycle batches / refinement steps
   bool use_graphs = true;
   cudaStream_t cap = nullptr;
@@ -470,31 +467,6 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw.omega_t = (float)h->opt.omega_tilde;
     sw.gscale = h->opt.variant == ADAFAC_VARIANT_EXP ? (float)h->opt.omega_exp : 1.0f;
     sw.variant = h->opt.variant;
-    // the small coarse levels in one launch
-    Coarse3Params& c3 = h->c3;
-    c3 = Coarse3Params();
-    c3.T = std::min(L - 1, kCoarse3Top);
-    c3.lmin = h->opt.lmin;
-    c3.variant = h->opt.variant;
-    c3.omega = (float)h->opt.omega;
-    c3.omega_t = (float)h->opt.omega_tilde;
-    for (int l = 1; l <= c3.T; ++l) {
-      c3.gscale[l] = h->opt.variant == ADAFAC_VARIANT_EXP
-                         ? (float)std::pow(h->opt.omega_exp, (double)(L - l))
-                         : 1.0f;
-      c3.r[l] = h->lev[l].r32;
-      c3.bt[l] = h->lev[l].bt32;
-      c3.g[l] = h->lev[l].g32;
-      c3.t[l] = h->lev[l].t32;
-      c3.invd[l] = h->lev[l].invd32;
-    }
-    for (int k = 0; k < 125; ++k) c3.stilde[k] = (float)sd[k];
-    c3.ctl = h->ctl;
-    c3.fault = &h->ctl->fault;
-    c3.fault_info = &h->ctl->fault_info[0];
-    coarse3_layout(&c3, &h->c3_bytes);
-    h->c3_ok = c3.T > c3.lmin && coarse3_prepare();
-    cudaGetLastError();
     // S~ by class (|oz|; in-plane distances); the class form is exact because
     // S~ is symmetric under reflections and permutations of the axes -- checked
     const int cls_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
@@ -687,30 +659,38 @@ void mixed_step(adafac_handle h, int k) {
 
 // Coarse levels L-1 .. 1 of an FP32 cycle whose level L-1 vectors came from a
 // fused sweep: restrictions below L-1, then the prolongation chain up to L-1.
-template <int D>
 void coarse_chain32(adafac_handle h) {
   const int L = h->L;
   const int lmin = h->opt.lmin;
   cudaStream_t s = h->stream;
   LevelData* lv = h->lev;
   const CycleParams<float>& cp = h->cp32;
-  // levels lmin .. T run in one launch when the fused kernel is available
-  const int T = h->c3_ok ? h->c3.T : lmin;
-  const int top = std::max(lmin, T);
-  for (int l = L - 2; l >= top; --l) {
-    const float gscale =
-        cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
-    launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
-                              lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
+  // the chain runs on the 3-D uniform path only: constant d-linear weights
+  Level3Params lp;
+  lp.variant = cp.variant;
+  lp.omega = cp.omega;
+  lp.omega_t = cp.omega_tilde;
+  for (int k = 0; k < 125; ++k) lp.stilde[k] = cp.stilde[k];
+  lp.ctl = h->ctl;
+  for (int l = L - 2; l >= lmin; --l) {
+    lp.nc = lv[l].n;
+    lp.nf = lv[l + 1].n;
+    lp.gscale = cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
+    lp.r_f = lv[l + 1].r32;
+    lp.r_c = lv[l].r32;
+    lp.bt_c = lv[l].bt32;
+    lp.g_c = lv[l].g32;
+    lp.invd_c = lv[l].invd32;
+    launch_restrict3u(lp, s);
     h->launches += 1;
   }
-  if (T > lmin) {
-    launch_coarse3(h->c3, h->c3_bytes, s);
-    h->launches += 1;
-  }
-  for (int l = top + 1; l <= L - 1; ++l) {
-    const float* tc = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
-    launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
+  for (int l = lmin + 1; l <= L - 1; ++l) {
+    lp.nc = lv[l - 1].n;
+    lp.nf = lv[l].n;
+    lp.t_c = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
+    lp.g_f = lv[l].g32;
+    lp.t_f = lv[l].t32;
+    launch_prolong3u(lp, s);
     h->launches += 1;
   }
 }
@@ -740,13 +720,13 @@ int fast3_step(adafac_handle h, int k, int ebase) {
   timed(h, ADAFAC_KERNEL_FINE_RESTRICT,
         [&] { launch_sweep3(p, h->maps, cur, SWEEP_UP, s); });
   h->launches += 1;
-  coarse_chain32<3>(h);
+  coarse_chain32(h);
   for (int j = 2; j <= k; ++j) {
     p.e_out = E[1 - cur];
     timed(h, ADAFAC_KERNEL_FINE_DOWN, [&] { launch_sweep3(p, h->maps, cur, SWEEP_DOWN, s); });
     timed(h, ADAFAC_KERNEL_FINE_UP, [&] { launch_sweep3(p, h->maps, 1 - cur, SWEEP_UPE, s); });
     h->launches += 2;
-    coarse_chain32<3>(h);
+    coarse_chain32(h);
     cur ^= 1;
   }
   p.e_out = E[1 - cur];

@@ -1,5 +1,6 @@
-// Shared-memory mbarriers and asynchronous bulk copies (sm_90 and later), with
-// waits that give up after a bounded time instead of spinning forever.
+// Shared-memory mbarriers for the tensor-memory-accelerator copies (sm_90 and
+// later), with waits that give up after a bounded time instead of spinning
+// forever.
 #pragma once
 
 #include <cstdint>
@@ -56,20 +57,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
   }
   return false;
-}
-
-// untiled bulk copy of `bytes` from global to shared memory, completing on the
-// mbarrier's transaction count; both addresses 16-byte aligned and `bytes` a
-// multiple of 16
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
-  uint64_t g;
-  asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(reinterpret_cast<uint64_t>(src)));
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(g), "r"(bytes), "r"(bar)
-      : "memory");
 }
 
 }  // namespace adafac

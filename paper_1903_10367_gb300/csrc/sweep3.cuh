@@ -77,32 +77,26 @@ void sweep3_grid(int nc, int zc, dim3* grid);       // up-passes (41 x 4 coarse 
 void sweep3_grid_down(int nc, int zc, dim3* grid);  // down-passes (64-column tiles)
 int refine3_blocks(int n, int zc);
 void launch_refine3(const Refine3Params& p, cudaStream_t s);
-// The coarse levels lmin .. T (T <= kCoarse3Top) of the 3-D uniform path in one
-// single-block launch (restrictions T -> lmin, then prolongations back to T).
-constexpr int kCoarse3Top = 3;  // largest fused level: 28^3 vertices
-struct Coarse3Params {
-  int T = 0, lmin = 1;
+// One restriction (level l + 1 -> l) or prolongation (l - 1 -> l) of the 3-D
+// uniform path's coarse levels, with the d-linear weights as constants: n_c /
+// n_f are the coarse / fine cell counts.
+struct Level3Params {
+  int nc = 0, nf = 0;
   int variant = V_JAC;
-  float omega = 0.6f, omega_t = 0.6f;
-  float gscale[kCoarse3Top + 1] = {};  // per level: omega_exp^(L - l) (exponential), else 1
-  float stilde[125] = {};              // truncated S~, x fastest
-  float* r[kCoarse3Top + 1] = {};
-  float* bt[kCoarse3Top + 1] = {};
-  float* g[kCoarse3Top + 1] = {};
-  float* t[kCoarse3Top + 1] = {};
-  const float* invd[kCoarse3Top + 1] = {};
+  float omega = 0.6f, omega_t = 0.6f, gscale = 1.0f;
+  float stilde[125] = {};
+  const float* r_f = nullptr;   // restriction: fine r
+  float* r_c = nullptr;         //   coarse r, b~, g
+  float* bt_c = nullptr;
+  float* g_c = nullptr;
+  const float* invd_c = nullptr;
+  const float* t_c = nullptr;   // prolongation: coarse t (or g on level lmin)
+  const float* g_f = nullptr;   //   fine g
+  float* t_f = nullptr;         //   fine t
   const Control* ctl = nullptr;
-  int* fault = nullptr;       // &ctl->fault: set when a bounded wait gives up
-  int* fault_info = nullptr;  // &ctl->fault_info[0]
-  // shared-memory layout in floats (coarse3_layout)
-  int off_r[kCoarse3Top + 1] = {}, off_t[kCoarse3Top + 1] = {};
-  int off_a = 0, off_b = 0;
 };
-// Fills the shared-memory offsets from T and lmin; *bytes = the block's need.
-void coarse3_layout(Coarse3Params* p, size_t* bytes);
-// Allows the largest layout's dynamic shared memory (once per process and device).
-bool coarse3_prepare();
-void launch_coarse3(const Coarse3Params& p, size_t smem_bytes, cudaStream_t s);
+void launch_restrict3u(const Level3Params& p, cudaStream_t s);
+void launch_prolong3u(const Level3Params& p, cudaStream_t s);
 
 // *out = max(*out, largest biased exponent of x[0 .. V)); skipped once halted
 void launch_max_exponent(const double* x, long long V, int* out, const Control* ctl,
