@@ -90,7 +90,15 @@ typedef struct {
                          allows them (3-D, scalar eps, d-linear, MIXED, CS form,
                          JAC/ADDITIVE/EXP with truncated R~), else one kernel
                          per level and step; ADAFAC_PATH_LEVELWISE: always the
-                         latter (same arithmetic, other summation order)      */
+                         latter (same arithmetic, other summation order).
+                         In MIXED precision the per-level kernels are shaped
+                         like the grids (a thread per vertex or coarse vertex,
+                         compile-time stencil offsets and weights);
+                         ADAFAC_PATH_GENERIC selects the generic per-level
+                         kernels instead (a linear index decoded per vertex,
+                         a warp per coarse vertex in the restriction): the
+                         same steps, another summation order.  FP64 cycles
+                         always use the generic kernels.                      */
   int coarse_op;      /* ADAFAC_COARSE_GALERKIN (default): A_{l-1} =
                          P_l^T A_l P_l (Sec. 2.2); ADAFAC_COARSE_REDISCRETISED:
                          the d-linear FEM operator of level l-1 with the eps of
@@ -100,7 +108,7 @@ typedef struct {
                          correction levels one by one below the finest)      */
 } adafac_options;
 
-enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1 };
+enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1, ADAFAC_PATH_GENERIC = 2 };
 enum { ADAFAC_COARSE_GALERKIN = 0, ADAFAC_COARSE_REDISCRETISED = 1 };
 
 /* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,

@@ -24,7 +24,7 @@ TRANSFER = {"dlinear": 0, "boxmg": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 RTILDE = {"truncated": 0, "exact": 1}
 FORM = {"cs": 0, "fas": 1}
-PATH = {"auto": 0, "levelwise": 1}
+PATH = {"auto": 0, "levelwise": 1, "generic": 2}
 FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
 COARSE = {"galerkin": 0, "rediscretised": 1}
 KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,

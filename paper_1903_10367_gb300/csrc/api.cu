@@ -22,6 +22,10 @@ namespace {
 constexpr int kHistCap = 8192;
 constexpr int kNormBlocks = 152 * 8;
 constexpr int kRefineZC = 16;    // fine planes per block of the 3-D refinement residual
+// coarse grids up to this many vertices take the warp-per-vertex restriction
+// in the mixed cycles: there a thread per coarse vertex leaves most of the
+// GPU idle and each thread's 5^d window is a long dependent chain
+constexpr long long kWarpRestrictMaxV = 4096;
 
 struct Graph {
   cudaGraphExec_t exec = nullptr;
@@ -153,7 +157,7 @@ bool valid_options(const adafac_options* o, std::string* why) {
   if (o->form == ADAFAC_FORM_FAS && o->precision != ADAFAC_PRECISION_FP64)
     return *why = "FAS form requires FP64 precision", false;
   if (o->inner_cycles < 1) return *why = "inner_cycles must be >= 1", false;
-  if (o->path < 0 || o->path > 1) return *why = "path out of range", false;
+  if (o->path < 0 || o->path > 2) return *why = "path out of range", false;
   if (o->coarse_op < 0 || o->coarse_op > 1) return *why = "coarse_op out of range", false;
   if (o->lmin < 1) return *why = "lmin must be >= 1", false;
   if (!(o->omega > 0.0) || !(o->omega_tilde >= 0.0) || !(o->omega_exp > 0.0))
@@ -251,11 +255,13 @@ void carve(adafac_handle h, Carver& cv) {
     h->rhs32 = cv.take<float>(Vp);
     if (h->fast3) h->e32b = cv.take<float>(Vp);
   }
+  // one norm partial per block of the refinement residual in use (the fused
+  // path may still fall back to the level kernels at setup)
   h->npartials = kNormBlocks;
-  if (h->fast3) {
-    const int nb = refine3_blocks(h->lev[L].n, kRefineZC);
-    h->npartials = nb > kNormBlocks ? nb : kNormBlocks;
-  }
+  if (h->fast3) h->npartials = std::max(h->npartials, refine3_blocks(h->lev[L].n, kRefineZC));
+  if (mixed)
+    h->npartials = std::max(h->npartials, D == 2 ? residual_g_blocks<2>(h->lev[L].n)
+                                                 : residual_g_blocks<3>(h->lev[L].n));
   h->partials = cv.take<double>(h->npartials);
   h->ctl = cv.take<Control>(1);
   h->hist = cv.take<double>(kHistCap);
@@ -595,7 +601,10 @@ void fp64_cycle(adafac_handle h) {
   h->launches += 1;
 }
 
-// One FP32 cycle on the correction equation A e = rhs32 (mixed mode).
+// One FP32 cycle on the correction equation A e = rhs32 (mixed mode): the
+// grid-shaped level kernels (level.cu), or with path GENERIC the generic
+// per-level kernels (cycle.cu).  The exact smoothed restriction, and the
+// restriction to small coarse grids, take the generic restriction.
 template <int D>
 void fp32_cycle(adafac_handle h) {
   const int L = h->L;
@@ -604,9 +613,14 @@ void fp32_cycle(adafac_handle h) {
   LevelData* lv = h->lev;
   const CycleParams<float>& cp = h->cp32;
   const bool exact = cp.rtilde_exact && cp.variant == V_JAC;
+  const bool grid = h->opt.path != ADAFAC_PATH_GENERIC;
   timed(h, ADAFAC_KERNEL_FINE_RESIDUAL, [&] {
-    launch_residual<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, nullptr,
-                                     0, 0.0, h->ctl, s);
+    if (grid)
+      launch_residual_g<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, 0.0,
+                                         h->ctl, s);
+    else
+      launch_residual<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, nullptr,
+                                       0, 0.0, h->ctl, s);
   });
   h->launches += 1;
   for (int l = L - 1; l >= lmin; --l) {
@@ -617,21 +631,35 @@ void fp32_cycle(adafac_handle h) {
       h->launches += 1;
     }
     timed(h, l + 1 == L ? ADAFAC_KERNEL_FINE_RESTRICT : ADAFAC_KERNEL_KINDS, [&] {
-      launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
-                                lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
+      // a thread per coarse vertex on large coarse grids; on small ones a warp
+      // per coarse vertex (its 32 lanes share the window) keeps more threads busy
+      if (grid && !exact && lv[l].V > kWarpRestrictMaxV)
+        launch_restrict_g<D>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l].r32, lv[l].bt32,
+                             lv[l].g32, gscale, h->ctl, s);
+      else
+        launch_restrict<D, float>(lv[l + 1].v32, lv[l].v32, cp, lv[l + 1].r32, lv[l + 1].y32,
+                                  lv[l].r32, 0, lv[l].bt32, lv[l].g32, gscale, h->ctl, s);
     });
     h->launches += 1;
   }
   for (int l = lmin + 1; l <= L - 1; ++l) {
     const float* tc = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
-    launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
+    if (grid)
+      launch_prolong_g<D, false>(lv[l].v32, lv[l - 1].v32, cp, nullptr, lv[l].g32, tc,
+                                 lv[l].t32, h->ctl, s);
+    else
+      launch_prolong<D, float>(lv[l].v32, lv[l - 1].v32, cp, tc, lv[l].g32, lv[l].t32, h->ctl, s);
     h->launches += 1;
   }
   LevelView<float> empty;
   const float* tc = L > lmin ? (L - 1 == lmin ? lv[lmin].g32 : lv[L - 1].t32) : nullptr;
   timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] {
-    launch_update<D, float, float>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, cp, lv[L].r32,
-                                   tc, h->e32, h->ctl, s);
+    if (grid)
+      launch_prolong_g<D, true>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, cp, lv[L].r32,
+                                nullptr, tc, h->e32, h->ctl, s);
+    else
+      launch_update<D, float, float>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, cp, lv[L].r32,
+                                     tc, h->e32, h->ctl, s);
   });
   h->launches += 1;
 }
@@ -641,11 +669,17 @@ void fp32_cycle(adafac_handle h) {
 template <int D>
 void refine_residual(adafac_handle h) {
   const int L = h->L;
+  const bool grid = h->opt.path != ADAFAC_PATH_GENERIC;
+  const int nb = grid ? residual_g_blocks<D>(h->lev[L].n) : kNormBlocks;
   timed(h, ADAFAC_KERNEL_REFINE, [&] {
-    launch_residual<D, double, double>(h->lev[L].v64, h->u, h->b, nullptr, h->rhs32,
-                                       h->partials, kNormBlocks, hD_of(h), h->ctl, h->stream);
+    if (grid)
+      launch_residual_g<D, double, float>(h->lev[L].v64, h->u, h->b, h->rhs32, h->partials,
+                                          hD_of(h), h->ctl, h->stream);
+    else
+      launch_residual<D, double, double>(h->lev[L].v64, h->u, h->b, nullptr, h->rhs32,
+                                         h->partials, kNormBlocks, hD_of(h), h->ctl, h->stream);
   });
-  launch_norm_finalize(h->partials, kNormBlocks, h->ctl, h->hist, kHistCap, 0, h->stream);
+  launch_norm_finalize(h->partials, nb, h->ctl, h->hist, kHistCap, 0, h->stream);
   h->launches += 2;
 }
 

@@ -134,6 +134,27 @@ template <int D>
 void launch_restrict_plain(const LevelView<double>& lf, const LevelView<double>& lc,
                            const double* r_f, double* b_c, const Control* ctl,
                            cudaStream_t s);
+// ---- grid-shaped level launches of the mixed-precision cycles (level.cu) ----
+// Blocks of the residual on a level with n cells (one norm partial per block).
+template <int D>
+int residual_g_blocks(int n);
+// r = b - A x on the finest level (OP_EPS or OP_UNIFORM), r zero on the
+// boundary; with partials: per-block sums of h^D r^2 in a fixed order.
+template <int D, typename T, typename TO>
+void launch_residual_g(const LevelView<T>& lv, const T* x, const T* b, TO* r,
+                       double* partials, double hD, const Control* ctl, cudaStream_t s);
+// r_c = P^T r_f, b~_c (truncated R~, JAC), g_c: one thread per coarse vertex.
+template <int D>
+void launch_restrict_g(const LevelView<float>& lf, const LevelView<float>& lc,
+                       const CycleParams<float>& cp, const float* r_f, float* r_c,
+                       float* bt_c, float* g_c, float gscale, const Control* ctl,
+                       cudaStream_t s);
+// UPDATE: x += omega M^-1 r_f + P q (finest level; counts the cycle);
+// else x = g_f + P q (coarse level t, zero on the boundary).
+template <int D, bool UPDATE>
+void launch_prolong_g(const LevelView<float>& lf, const LevelView<float>& lc,
+                      const CycleParams<float>& cp, const float* r_f, const float* g_f,
+                      const float* t_c, float* x, Control* ctl, cudaStream_t s);
 // Sums the partials of one norm evaluation (fixed order), records history,
 // sets done / diverged.
 // query != 0: only qsq/qrel (and r_0 when set_r0) are written, regardless of
