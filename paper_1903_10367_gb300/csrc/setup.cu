@@ -325,9 +325,28 @@ __device__ double closure_weight(const LevelView<double>& fine, int n_c, const i
   return fine.P[(long long)eo * fine.V + encode<D>(fc, fine.np1)];
 }
 
+// Structural zeros of the closure weights: the weight of closure point l
+// (coordinates 0..3 in the coarse cell) towards corner f vanishes along any
+// axis where the point lies on the cell face opposite the corner (l_j = 0
+// and f_j = 1, or l_j = 3 and f_j = 0), for d-linear and BoxMG weights alike.
+template <int D>
+__device__ __forceinline__ bool closure_zero(const int* l, int f) {
+  bool z = false;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const int bit = (f >> j) & 1;
+    z = z || (l[j] == 0 && bit) || (l[j] == 3 && !bit);
+  }
+  return z;
+}
+
 // Galerkin element matrices of the coarse level: K_E = sum over the 3^D
 // children c of P_c^T K_c P_c (one thread per coarse cell).  The fine element
-// matrices are eps_c h^(D-2) K_ref (fine level) or stored (Kc_fine).
+// matrices are eps_c h^(D-2) K_ref (fine level) or stored (Kc_fine).  FP64
+// work is the cost here, so the products skip the terms that vanish by
+// structure: the structural zeros of the closure weights, the zero entries
+// of K_ref (in 3-D, corners one edge apart), and the lower triangle of the
+// symmetric K_E (filled by symmetry at the end).
 template <int D>
 __global__ void __launch_bounds__(128) k_galerkin(LevelView<double> fine, const double* __restrict__ Kc_fine,
                                                   double* __restrict__ Kc, int n_c) {
@@ -360,40 +379,49 @@ __global__ void __launch_bounds__(128) k_galerkin(LevelView<double> fine, const 
     }
     const long long cidx = encode<D>(child, n_f);
     double Kf[NC * NC];
+    const double eh = Kc_fine ? 0.0 : (fine.opkind == OP_EPS ? fine.eps[cidx] : fine.eps0) * fine.hfac;
+#pragma unroll
     for (int a = 0; a < NC; ++a)
-      for (int b = 0; b < NC; ++b) {
-        double val;
-        if (Kc_fine) {
-          val = Kc_fine[(long long)(a * NC + b) * ncf + cidx];
-        } else {
-          const double e = fine.opkind == OP_EPS ? fine.eps[cidx] : fine.eps0;
-          val = e * fine.hfac * kref<D, double>(__popc(a ^ b));
-        }
-        Kf[a * NC + b] = val;
-      }
+#pragma unroll
+      for (int b = 0; b < NC; ++b)
+        Kf[a * NC + b] = Kc_fine ? Kc_fine[(long long)(a * NC + b) * ncf + cidx]
+                                 : eh * kref<D, double>(__popc(a ^ b));
     // T = Kf * Pc  (Pc[b][f] = W[kc + b][f])
     double Tm[NC * NC];
+#pragma unroll
     for (int a = 0; a < NC; ++a)
+#pragma unroll
       for (int f = 0; f < NC; ++f) {
         double s = 0.0;
+#pragma unroll
         for (int b = 0; b < NC; ++b) {
+          if (!Kc_fine && D == 3 && __popc(a ^ b) == 1) continue;  // K_ref entry 0
           int lb[D];
           for (int j = 0; j < D; ++j) lb[j] = kc[j] + ((b >> j) & 1);
+          if (closure_zero<D>(lb, f)) continue;
           s += Kf[a * NC + b] * W[encode<D>(lb, 4) * NC + f];
         }
         Tm[a * NC + f] = s;
       }
+    // K += Pc^T T on the upper triangle (e <= f)
+#pragma unroll
     for (int a = 0; a < NC; ++a) {
       int la[D];
       for (int j = 0; j < D; ++j) la[j] = kc[j] + ((a >> j) & 1);
       const int pa = encode<D>(la, 4);
+#pragma unroll
       for (int e = 0; e < NC; ++e) {
+        if (closure_zero<D>(la, e)) continue;
         const double wae = W[pa * NC + e];
-        if (wae == 0.0) continue;
-        for (int f = 0; f < NC; ++f) K[e * NC + f] += wae * Tm[a * NC + f];
+#pragma unroll
+        for (int f = e; f < NC; ++f) K[e * NC + f] += wae * Tm[a * NC + f];
       }
     }
   }
+#pragma unroll
+  for (int e = 0; e < NC; ++e)
+#pragma unroll
+    for (int f = 0; f < e; ++f) K[e * NC + f] = K[f * NC + e];
   for (int i = 0; i < NC * NC; ++i) Kc[(long long)i * total + E] = K[i];
 }
 
