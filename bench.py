@@ -203,6 +203,20 @@ def _needs_flush(w, precision):
     return (3 ** w.depth + 1) ** w.dim * per < 2 * L2_BYTES
 
 
+def _tuning_summary(t):
+    """The launch shapes the autotuner chose (None when it was not run)."""
+    if not t:
+        return None
+    if t["path"] == 1:
+        shapes = {"sweep_zc": t["sweep_zc"], "sweep_zc_down": t["sweep_zc_down"]}
+    elif t["path"] == 2:
+        shapes = {k: t[k] for k in ("res_bx", "res_by", "res_zr", "upd_bx", "upd_by")}
+    else:
+        shapes = {}
+    return dict(shapes, candidates=t["candidates"], us_default=round(t["us_default"], 2),
+                us_tuned=round(t["us_tuned"], 2))
+
+
 def _config(w, args, cycles):
     return {"workload": w.name, "dim": w.dim, "depth": w.depth,
             "fine_dofs": (3 ** w.depth - 1) ** w.dim, "dofs_all_levels": sum(w.level_dofs()),
@@ -231,6 +245,9 @@ def bench_ours(args, w):
     eps_arg = float(eps[0]) if sc else eps
     opts = adafac.default_options(transfer=w.transfer, precision=args.precision)
     S = adafac.Solver(w.dim, w.depth, eps_arg, f, opts)
+    # launch shapes of the fine-level kernels chosen by the library's autotuner
+    # (timed here once; later handles of this shape take the stored choice)
+    tuning = None if args.no_autotune else S.autotune(5)
     upd_cycle = sum(w.level_dofs())
     # warm-up: full solves; the cycle count of one solve defines a step
     cycles = None
@@ -293,7 +310,7 @@ def bench_ours(args, w):
     peaks, src = _peaks()
     alg = _algorithmic_bytes(dom, w, args.precision, sc)
     achieved = alg / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
-    traffic = _traffic_from_profile(dom, w)
+    traffic = _traffic_from_profile(dom, w, tuning)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"] if achieved else None,
                 "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
@@ -319,7 +336,7 @@ def bench_ours(args, w):
                 "value": c64 * upd_cycle / (e0.elapsed_time(e1) / 1e3), "unit": UNIT}
         S64.close()
     # end to end through the public API from pinned host buffers
-    e2e = _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch)
+    e2e = _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch, tuning is not None)
     S.close()
     if rank != 0:
         return
@@ -329,7 +346,7 @@ def bench_ours(args, w):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 cycles + f64 refinement" if args.precision == "mixed" else "f64",
-           "data": "synthetic", "config": _config(w, args, cycles),
+           "data": "synthetic", "config": dict(_config(w, args, cycles), tuning=_tuning_summary(tuning)),
            "time_to_tol_ms": ms / args.steps, "e2e": e2e, "gpu_launches": launches,
            "roofline": roofline, "clocks": clk, "cpu_baseline": cpu,
            "fp64_comparator": fp64, "serving": serving}
@@ -338,8 +355,9 @@ def bench_ours(args, w):
         dist.destroy_process_group()
 
 
-def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch):
-    """Setup from host buffers, solve to the tolerance, read the solution back."""
+def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch, tune):
+    """Setup from host buffers, solve to the tolerance, read the solution back
+    (with the autotuner's stored launch shapes when the bench tuned them)."""
     if args.e2e_steps <= 0:
         return None
     f_pin = torch.from_numpy(f).pin_memory()
@@ -353,6 +371,8 @@ def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch):
         t0 = time.perf_counter()
         S = adafac.Solver(w.dim, w.depth, float(eps[0]) if sc else eps_pin.numpy(),
                           f_pin.numpy(), opts, workspace=ws)
+        if tune:
+            S.autotune(5)
         c, rel = S.solve(args.tol, args.max_cycles)
         S.solution(out.numpy())
         t1 = time.perf_counter()
@@ -363,7 +383,8 @@ def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch):
     h2d = f.nbytes + (8 if sc else eps.nbytes)
     return {"value": cycles * upd_cycle / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(f.nbytes), "ms_per_step": 1e3 * t,
-            "includes": "setup (H2D copies, BoxMG/Galerkin), solve to tol, D2H of u"}
+            "includes": "setup (H2D copies, BoxMG/Galerkin), stored launch shapes, solve to tol, "
+                        "D2H of u"}
 
 
 def kernel_source_hash():
@@ -462,17 +483,22 @@ def run_serving(count: int, seed: int = 1903):
     }
 
 
-def _traffic_from_profile(kind, w):
+def _traffic_from_profile(kind, w, tuning=None):
     """DRAM bytes (read + write) per launch of this kernel from the committed
     ncu summary (profiles/traffic.json), or None when the summary was taken on
-    other kernel sources."""
+    other kernel sources or with other tile depths of the sweeps."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             table = json.load(fh)
         if table.get("source_hash") != kernel_source_hash():
             return None
-        return table.get(w.name, {}).get(kind)
+        entry = table.get(w.name, {})
+        if tuning and tuning.get("path") == 1 and "sweep_zc" in entry:
+            if (entry["sweep_zc"], entry["sweep_zc_down"]) != (tuning["sweep_zc"],
+                                                               tuning["sweep_zc_down"]):
+                return None
+        return entry.get(kind)
     except Exception:
         return None
 
@@ -491,6 +517,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-comparator", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of the autotuned ones")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving stream run after the solve (0: skip)")
     args = ap.parse_args()

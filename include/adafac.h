@@ -255,6 +255,46 @@ adafac_status adafac_timing(adafac_handle h, int enable);
 adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
                                  int* launches);
 
+/* ---- Autotuner of tile and launch shapes ---------------------------------
+ *
+ * Performance extension; the paper has no counterpart (its cycle runs on a
+ * CPU spacetree traversal).  adafac_autotune times candidate shapes of the
+ * handle's dominant fine-level kernels on the handle's own arrays and keeps
+ * the fastest (a candidate replaces the default only when it is at least 2 %
+ * faster):
+ *   path 1, the fused 3-D sweeps (MIXED, scalar eps, d-linear, 3-D): the
+ *     depth of the up-pass and down-pass tiles in coarse planes per block
+ *     (sweep_zc, sweep_zc_down: every distinct ceil((3^(L-1)+1) / chunks)
+ *     from 3 to 24);
+ *   path 2, the grid-shaped level kernels (MIXED otherwise, path not
+ *     GENERIC): the block shape of the fine residual and of the fine update
+ *     (res_bx x res_by, upd_bx x upd_by threads from 32x8, 64x4, 32x4,
+ *     128x2, 64x2, 256x1) and the length of the residual's z columns
+ *     (res_zr planes, 0 = the size rule; 3-D only);
+ *   path 0: nothing to tune (FP64 precision or path GENERIC).
+ * Every shape computes the same values: solutions, norms and cycle counts do
+ * not change.  Each candidate is timed over `repeats` launches (1..1000)
+ * after one untimed launch.  Results are kept per process, device and
+ * problem shape (dim, depth, path, eps kind, transfer, variant, lmin): a later
+ * handle of the same shape takes them without timing (cached = 1).
+ * The call synchronises the handle's stream, runs only on the handle's
+ * arrays, and resets the cycle state (control block, history, correction
+ * buffers; not the iterate u): call it after setup and before cycling.
+ * Returns INVALID_ARG (null argument, repeats out of range) or CUDA. */
+typedef struct {
+  int path;            /* 0 nothing tuned, 1 fused 3-D sweeps, 2 level kernels */
+  int cached;          /* 1: taken from an earlier tuning of the same shape   */
+  int sweep_zc;        /* path 1: coarse planes per block of the up-passes    */
+  int sweep_zc_down;   /* path 1: coarse planes per block of the down-passes  */
+  int res_bx, res_by;  /* path 2: threads per block of the fine residual      */
+  int res_zr;          /* path 2: planes per thread column (0 = size rule)    */
+  int upd_bx, upd_by;  /* path 2: threads per block of the fine update        */
+  int candidates;      /* launch shapes timed                                 */
+  double us_default;   /* one launch each of the tuned kernels, default shapes, us */
+  double us_tuned;     /* the same with the chosen shapes, us                 */
+} adafac_tuning;
+adafac_status adafac_autotune(adafac_handle h, int repeats, adafac_tuning* out);
+
 /* ||b - A u||_h (Eq. 10) for the uniform d-linear operator of
  * -div(eps grad u) with scalar eps (Sec. 2.1) on a regular tree of depth
  * `depth` in `dim` = 2 or 3 dimensions, computed WITHOUT ALLOCATING device

@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "AdafacError", "Tree", "Options", "load", "default_options", "workspace_size",
+    "AdafacError", "Tree", "Options", "Tuning", "load", "default_options", "workspace_size",
     "Solver", "FIELD", "VARIANT", "TRANSFER", "PRECISION", "RTILDE", "FORM",
 ]
 
@@ -52,6 +52,14 @@ class RequestInfo(ctypes.Structure):
 REQUEST_STATE = {0: "pending", 1: "running", 2: "done", 3: "failed"}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("cached", ctypes.c_int), ("sweep_zc", ctypes.c_int),
+                ("sweep_zc_down", ctypes.c_int), ("res_bx", ctypes.c_int),
+                ("res_by", ctypes.c_int), ("res_zr", ctypes.c_int), ("upd_bx", ctypes.c_int),
+                ("upd_by", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("us_default", ctypes.c_double), ("us_tuned", ctypes.c_double)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("transfer", ctypes.c_int),
                 ("precision", ctypes.c_int), ("rtilde", ctypes.c_int),
@@ -85,6 +93,7 @@ _SIGNATURES = [
     ("adafac_launch_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     ("adafac_timing", _I, [_P, _I]),
     ("adafac_timing_read", _I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    ("adafac_autotune", _I, [_P, _I, ctypes.POINTER(Tuning)]),
     ("adafac_residual_norm_static", _I, [_I, _I, _D, _P, _P, _P, _P]),
     ("adafac_server_create", _I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
     ("adafac_submit", _I, [_P, ctypes.POINTER(Tree), _P, _I, _P, ctypes.POINTER(Options), _D,
@@ -301,6 +310,13 @@ class Solver:
         _check(self.lib.adafac_timing_read(self.h, KERNEL[kind], ctypes.byref(ms),
                                            ctypes.byref(n)), self.h)
         return ms.value, n.value
+
+    def autotune(self, repeats: int = 5) -> dict:
+        """Times candidate launch shapes of the fine-level kernels and keeps
+        the fastest (adafac_autotune); returns the tuning record."""
+        t = Tuning()
+        _check(self.lib.adafac_autotune(self.h, int(repeats), ctypes.byref(t)), self.h)
+        return {name: getattr(t, name) for name, _ in Tuning._fields_}
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

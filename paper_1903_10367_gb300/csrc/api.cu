@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -104,6 +106,8 @@ struct adafac_handle_s {
   Sweep3Maps maps;
   Sweep3Params sw;
   Refine3Params rf;
+  // launch shapes of the fine residual and update of the level path (autotuned)
+  GridShape res_shape, upd_shape;
   // CUDA graphs of whole cycle batches / refinement steps
   bool use_graphs = true;
   cudaStream_t cap = nullptr;
@@ -617,7 +621,7 @@ void fp32_cycle(adafac_handle h) {
   timed(h, ADAFAC_KERNEL_FINE_RESIDUAL, [&] {
     if (grid)
       launch_residual_g<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, 0.0,
-                                         h->ctl, s);
+                                         h->ctl, s, h->res_shape);
     else
       launch_residual<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, nullptr,
                                        0, 0.0, h->ctl, s);
@@ -656,7 +660,7 @@ void fp32_cycle(adafac_handle h) {
   timed(h, ADAFAC_KERNEL_FINE_UPDATE, [&] {
     if (grid)
       launch_prolong_g<D, true>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, cp, lv[L].r32,
-                                nullptr, tc, h->e32, h->ctl, s);
+                                nullptr, tc, h->e32, h->ctl, s, h->upd_shape);
     else
       launch_update<D, float, float>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, cp, lv[L].r32,
                                      tc, h->e32, h->ctl, s);
@@ -925,6 +929,160 @@ adafac_status handle_arm(adafac_handle h, double rel_tol) {
 }
 
 }  // namespace adafac
+
+// ---- autotuner helpers -----------------------------------------------------------
+namespace {
+
+// Tuned shapes of the process, by device and problem shape: a handle whose
+// shape was tuned before takes the stored result without timing.
+struct TuneKey {
+  int dev, D, L, fast3, opkind, boxmg, variant, lmin;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, D, L, fast3, opkind, boxmg, variant, lmin) <
+           std::tie(o.dev, o.D, o.L, o.fast3, o.opkind, o.boxmg, o.variant, o.lmin);
+  }
+};
+std::mutex g_tune_lock;
+std::map<TuneKey, adafac_tuning> g_tune_cache;
+
+// Mean device time of `reps` launches (after one untimed launch), in us.
+template <typename F>
+double time_us(adafac_handle h, int reps, F&& launch) {
+  cudaEvent_t a = next_event(h), b = next_event(h);
+  launch();
+  cudaEventRecord(a, h->stream);
+  for (int i = 0; i < reps; ++i) launch();
+  cudaEventRecord(b, h->stream);
+  float ms = 0.0f;
+  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+    return -1.0;
+  h->ev_used -= 2;
+  return 1e3 * ms / reps;
+}
+
+// Coarse planes per block of the fused sweeps worth timing: every distinct
+// ceil(ncp1 / chunks) from 3 up to 24.
+std::vector<int> zc_candidates(int ncp1) {
+  std::vector<int> out;
+  for (int chunks = 1; chunks <= ncp1; ++chunks) {
+    const int zc = std::max(3, (ncp1 + chunks - 1) / chunks);
+    if (zc <= 24 && std::find(out.begin(), out.end(), zc) == out.end()) out.push_back(zc);
+  }
+  return out;
+}
+
+template <int D>
+adafac_status tune_level(adafac_handle h, int reps, adafac_tuning* t) {
+  const int L = h->L, lmin = h->opt.lmin;
+  LevelData* lv = h->lev;
+  cudaStream_t s = h->stream;
+  const float* tc = L > lmin ? (L - 1 == lmin ? lv[lmin].g32 : lv[L - 1].t32) : nullptr;
+  LevelView<float> empty;
+  auto res = [&](GridShape g) {
+    return time_us(h, reps, [&] {
+      launch_residual_g<D, float, float>(lv[L].v32, h->e32, h->rhs32, lv[L].r32, nullptr, 0.0,
+                                         h->ctl, s, g);
+    });
+  };
+  auto upd = [&](GridShape g) {
+    return time_us(h, reps, [&] {
+      launch_prolong_g<D, true>(lv[L].v32, L > lmin ? lv[L - 1].v32 : empty, h->cp32, lv[L].r32,
+                                nullptr, tc, h->e32, h->ctl, s, g);
+    });
+  };
+  const int shapes[6][2] = {{32, 8}, {64, 4}, {32, 4}, {128, 2}, {64, 2}, {256, 1}};
+  const int zrs[6] = {0, 2, 4, 8, 16, 32};
+  const double res0 = res(GridShape()), upd0 = upd(GridShape());
+  if (res0 < 0.0 || upd0 < 0.0) return check_cuda(h, "autotune timing");
+  double best_res = res0, best_upd = upd0;
+  GridShape g_res, g_upd;
+  int timed = 2;
+  for (const auto& sh : shapes) {
+    for (int zr : zrs) {
+      if (D == 2 && zr != 0) continue;
+      if (zr > lv[L].n + 1) continue;
+      GridShape g;
+      g.bx = sh[0];
+      g.by = sh[1];
+      g.zr = zr;
+      const double us = res(g);
+      ++timed;
+      if (us > 0.0 && us < best_res) best_res = us, g_res = g;
+    }
+    GridShape g;
+    g.bx = sh[0];
+    g.by = sh[1];
+    const double us = upd(g);
+    ++timed;
+    if (us > 0.0 && us < best_upd) best_upd = us, g_upd = g;
+  }
+  // keep the default unless the gain is clear of the timing noise
+  if (best_res > 0.98 * res0) g_res = GridShape(), best_res = res0;
+  if (best_upd > 0.98 * upd0) g_upd = GridShape(), best_upd = upd0;
+  h->res_shape = g_res;
+  h->upd_shape = g_upd;
+  t->path = 2;
+  t->res_bx = g_res.bx ? g_res.bx : 32;
+  t->res_by = g_res.by ? g_res.by : 8;
+  t->res_zr = g_res.zr;
+  t->upd_bx = g_upd.bx ? g_upd.bx : 32;
+  t->upd_by = g_upd.by ? g_upd.by : 8;
+  t->candidates = timed;
+  t->us_default = res0 + upd0;
+  t->us_tuned = best_res + best_upd;
+  return check_cuda(h, "autotune");
+}
+
+adafac_status tune_fast3(adafac_handle h, int reps, adafac_tuning* t) {
+  const int L = h->L, lmin = h->opt.lmin;
+  cudaStream_t s = h->stream;
+  Sweep3Params p = h->sw;
+  p.q = L - 1 == lmin ? h->lev[lmin].g32 : h->lev[L - 1].t32;
+  p.e_out = h->e32b;
+  auto sweep = [&](int mode, int zc) {
+    Sweep3Params q = p;
+    if (mode == SWEEP_UPE) q.zc = zc;
+    else q.zc_down = zc;
+    return time_us(h, reps, [&] { launch_sweep3(q, h->maps, mode == SWEEP_UPE ? 1 : 0, mode, s); });
+  };
+  const int ncp1 = h->lev[L - 1].n + 1;
+  const double up0 = sweep(SWEEP_UPE, p.zc), down0 = sweep(SWEEP_DOWN, p.zc_down);
+  if (up0 < 0.0 || down0 < 0.0) return check_cuda(h, "autotune timing");
+  double best_up = up0, best_down = down0;
+  int zc = p.zc, zcd = p.zc_down, timed = 2;
+  for (int c : zc_candidates(ncp1)) {
+    const double u = sweep(SWEEP_UPE, c), d = sweep(SWEEP_DOWN, c);
+    timed += 2;
+    if (u > 0.0 && u < best_up) best_up = u, zc = c;
+    if (d > 0.0 && d < best_down) best_down = d, zcd = c;
+  }
+  if (best_up > 0.98 * up0) zc = p.zc, best_up = up0;
+  if (best_down > 0.98 * down0) zcd = p.zc_down, best_down = down0;
+  h->sw.zc = zc;
+  h->sw.zc_down = zcd;
+  t->path = 1;
+  t->sweep_zc = zc;
+  t->sweep_zc_down = zcd;
+  t->candidates = timed;
+  t->us_default = up0 + down0;
+  t->us_tuned = best_up + best_down;
+  return check_cuda(h, "autotune");
+}
+
+void apply_tuning(adafac_handle h, const adafac_tuning& t) {
+  if (t.path == 1) {
+    h->sw.zc = t.sweep_zc;
+    h->sw.zc_down = t.sweep_zc_down;
+  } else if (t.path == 2) {
+    h->res_shape.bx = t.res_bx;
+    h->res_shape.by = t.res_by;
+    h->res_shape.zr = t.res_zr;
+    h->upd_shape.bx = t.upd_bx;
+    h->upd_shape.by = t.upd_by;
+  }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1308,6 +1466,47 @@ adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms, in
 
 const char* adafac_last_error(adafac_handle h) {
   return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+adafac_status adafac_autotune(adafac_handle h, int repeats, adafac_tuning* out) {
+  if (!h || !out) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  if (repeats < 1 || repeats > 1000) return fail(h, ADAFAC_ERR_INVALID_ARG, "repeats must be in 1..1000");
+  *out = adafac_tuning();
+  const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
+  const bool level = mixed && !h->fast3 && h->opt.path != ADAFAC_PATH_GENERIC;
+  if (!h->fast3 && !level) return ADAFAC_OK;  // nothing tunable: path 0
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda(h, "autotune device");
+  const TuneKey key{dev, h->D, h->L, h->fast3 ? 1 : 0, h->lev[h->L].v32.opkind,
+                    h->opt.transfer, h->opt.variant, h->opt.lmin};
+  {
+    std::lock_guard<std::mutex> g(g_tune_lock);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *out = it->second;
+      out->cached = 1;
+      apply_tuning(h, *out);
+      for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+      h->graphs.clear();
+      return ADAFAC_OK;
+    }
+  }
+  // the timed kernels must run: clear the converged / diverged flags first
+  adafac_status st = reset_control(h);
+  if (st != ADAFAC_OK) return st;
+  if (h->fast3) st = tune_fast3(h, repeats, out);
+  else st = h->D == 2 ? tune_level<2>(h, repeats, out) : tune_level<3>(h, repeats, out);
+  if (st != ADAFAC_OK) return st;
+  // graphs captured with the old shapes are dropped; the timed launches wrote
+  // the correction buffers and counted cycles: start the cycle state afresh
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+  st = reset_control(h);
+  if (st != ADAFAC_OK) return st;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "autotune");
+  std::lock_guard<std::mutex> g(g_tune_lock);
+  g_tune_cache[key] = *out;
+  return ADAFAC_OK;
 }
 
 adafac_status adafac_destroy(adafac_handle h) {

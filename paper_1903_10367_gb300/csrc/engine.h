@@ -135,6 +135,13 @@ void launch_restrict_plain(const LevelView<double>& lf, const LevelView<double>&
                            const double* r_f, double* b_c, const Control* ctl,
                            cudaStream_t s);
 // ---- grid-shaped level launches of the mixed-precision cycles (level.cu) ----
+// Launch shape of a vertex-grid kernel: bx x by threads (whole warps, at most
+// 256), zr planes per thread column of the 3-D residual (0: a size rule);
+// bx = by = 0 takes 32 x 8.  The arithmetic of every vertex is the same for
+// every shape.
+struct GridShape {
+  int bx = 0, by = 0, zr = 0;
+};
 // Blocks of the residual on a level with n cells (one norm partial per block).
 template <int D>
 int residual_g_blocks(int n);
@@ -142,7 +149,8 @@ int residual_g_blocks(int n);
 // boundary; with partials: per-block sums of h^D r^2 in a fixed order.
 template <int D, typename T, typename TO>
 void launch_residual_g(const LevelView<T>& lv, const T* x, const T* b, TO* r,
-                       double* partials, double hD, const Control* ctl, cudaStream_t s);
+                       double* partials, double hD, const Control* ctl, cudaStream_t s,
+                       GridShape shape = GridShape());
 // r_c = P^T r_f, b~_c (truncated R~, JAC), g_c: one thread per coarse vertex.
 template <int D>
 void launch_restrict_g(const LevelView<float>& lf, const LevelView<float>& lc,
@@ -154,7 +162,8 @@ void launch_restrict_g(const LevelView<float>& lf, const LevelView<float>& lc,
 template <int D, bool UPDATE>
 void launch_prolong_g(const LevelView<float>& lf, const LevelView<float>& lc,
                       const CycleParams<float>& cp, const float* r_f, const float* g_f,
-                      const float* t_c, float* x, Control* ctl, cudaStream_t s);
+                      const float* t_c, float* x, Control* ctl, cudaStream_t s,
+                      GridShape shape = GridShape());
 // Sums the partials of one norm evaluation (fixed order), records history,
 // sets done / diverged.
 // query != 0: only qsq/qrel (and r_0 when set_r0) are written, regardless of

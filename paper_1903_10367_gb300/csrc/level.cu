@@ -31,7 +31,8 @@ namespace adafac {
 
 namespace {
 
-constexpr int FX = 32, FY = 8;   // threads per block on vertex grids (x, y)
+constexpr int FX = 32, FY = 8;   // default threads per block on vertex grids (x, y)
+constexpr int kMaxThreads = 256; // largest block of the vertex-grid kernels
 constexpr int ZRMAX = 16;        // most planes per thread column of the 3-D residual
 constexpr int CX = 32, CY = 4;   // threads per block of the restriction (x, y)
 
@@ -40,30 +41,37 @@ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 // Planes per thread column of the 3-D residual: long columns (fewer plane
 // reloads) as long as the grid still has about two blocks per SM of a
 // 152-SM GPU; one plane per column on small grids.
-inline int residual_zr(int np1) {
-  const int xy = cdiv(np1, FX) * cdiv(np1, FY);
+inline int residual_zr(int np1, int bx = FX, int by = FY) {
+  const int xy = cdiv(np1, bx) * cdiv(np1, by);
   const int zr = np1 * xy / (2 * 152);
   return zr < 1 ? 1 : (zr > ZRMAX ? ZRMAX : zr);
 }
 
 template <int D>
-inline int zblocks_residual(int np1) {
-  return D == 3 ? cdiv(np1, residual_zr(np1)) : 1;
+inline int zblocks_residual(int np1, int zr) {
+  return D == 3 ? cdiv(np1, zr) : 1;
+}
+
+// The launch shape actually used: zr = 0 takes the size rule above.
+inline GridShape resolve(GridShape g, int np1) {
+  if (g.bx <= 0 || g.by <= 0) g.bx = FX, g.by = FY;
+  if (g.zr <= 0) g.zr = residual_zr(np1, g.bx, g.by);
+  return g;
 }
 
 // Block sum of acc in a fixed order (warp shuffles, then the warps in order),
 // written to partials[block] scaled by hD.
 __device__ __forceinline__ void block_partial(double acc, double hD, double* partials) {
-  __shared__ double red[FX * FY / 32];
+  __shared__ double red[kMaxThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  const int t = threadIdx.y * FX + threadIdx.x;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nw = (blockDim.x * blockDim.y) >> 5;  // block shapes are whole warps
   if ((t & 31) == 0) red[t >> 5] = acc;
   __syncthreads();
   if (t == 0) {
     double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < FX * FY / 32; ++w) s += red[w];
+    for (int w = 0; w < nw; ++w) s += red[w];
     partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s * hD;
   }
 }
@@ -75,14 +83,14 @@ __device__ __forceinline__ void block_partial(double acc, double hD, double* par
 // + sx, y - 1 + sy).  For the cell on side (sx, sy, sz) the corners without a
 // shared cell edge are (sx, sy, 0), (sx, 0, sz), (0, sy, sz), (sx, sy, sz).
 template <typename T, typename TO, bool EPS, bool NORM>
-__global__ void __launch_bounds__(FX* FY)
+__global__ void __launch_bounds__(kMaxThreads)
     k_residual3g(const LevelView<T> lv, const T* __restrict__ x, const T* __restrict__ b,
                  TO* __restrict__ r, double* __restrict__ partials, double hD, int zr,
                  const Control* ctl) {
   if (halted(ctl)) return;
   constexpr T K0 = T(1.0 / 3.0), KD = T(-1.0 / 12.0);
   const int n = lv.n, np1 = n + 1;
-  const int ix = blockIdx.x * FX + threadIdx.x, iy = blockIdx.y * FY + threadIdx.y;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y * blockDim.y + threadIdx.y;
   const int z0 = blockIdx.z * zr, z1 = min(z0 + zr, np1);
   const int P = np1 * np1;
   double acc = 0.0;
@@ -168,14 +176,14 @@ __global__ void __launch_bounds__(FX* FY)
 // 2-D residual: one thread per vertex.  For the cell on side (sx, sy) the
 // corners at Hamming distance 1 are (sx, 0) and (0, sy), at distance 2 (sx, sy).
 template <typename T, typename TO, bool EPS, bool NORM>
-__global__ void __launch_bounds__(FX* FY)
+__global__ void __launch_bounds__(kMaxThreads)
     k_residual2g(const LevelView<T> lv, const T* __restrict__ x, const T* __restrict__ b,
                  TO* __restrict__ r, double* __restrict__ partials, double hD,
                  const Control* ctl) {
   if (halted(ctl)) return;
   constexpr T K0 = T(2.0 / 3.0), K1 = T(-1.0 / 6.0), K2 = T(-1.0 / 3.0);
   const int n = lv.n, np1 = n + 1;
-  const int ix = blockIdx.x * FX + threadIdx.x, iy = blockIdx.y * FY + threadIdx.y;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y * blockDim.y + threadIdx.y;
   double acc = 0.0;
   if (ix <= n && iy <= n) {
     const int v = iy * np1 + ix;
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(CX* CY)
 // corners with e_j = 1 (for BoxMG as for d-linear weights): those corners are
 // skipped; every other corner is summed, also where its weight is zero.
 template <int D, bool UPDATE, bool BOXMG, bool PI>
-__global__ void __launch_bounds__(FX* FY)
+__global__ void __launch_bounds__(kMaxThreads)
     k_prolong_g(const LevelView<float> lf, const LevelView<float> lc, const CycleParams<float> cp,
                 const float* __restrict__ r_f, const float* __restrict__ g_f,
                 const float* __restrict__ t_c, float* __restrict__ x, Control* ctl) {
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(FX* FY)
       threadIdx.x == 0 && threadIdx.y == 0)
     atomicAdd(&ctl->applied, 1);
   const int n = lf.n, np1 = n + 1;
-  const int c[3] = {(int)(blockIdx.x * FX + threadIdx.x), (int)(blockIdx.y * FY + threadIdx.y),
+  const int c[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
                     D == 3 ? (int)blockIdx.z : 0};
   if (c[0] > n || c[1] > n) return;
   const int v = (c[2] * np1 + c[1]) * np1 + c[0];
@@ -364,17 +372,19 @@ __global__ void __launch_bounds__(FX* FY)
 template <int D>
 int residual_g_blocks(int n) {
   const int np1 = n + 1;
-  return cdiv(np1, FX) * cdiv(np1, FY) * zblocks_residual<D>(np1);
+  const GridShape g = resolve(GridShape(), np1);
+  return cdiv(np1, g.bx) * cdiv(np1, g.by) * zblocks_residual<D>(np1, g.zr);
 }
 
 template <int D, typename T, typename TO>
 void launch_residual_g(const LevelView<T>& lv, const T* x, const T* b, TO* r, double* partials,
-                       double hD, const Control* ctl, cudaStream_t s) {
+                       double hD, const Control* ctl, cudaStream_t s, GridShape shape) {
   const int np1 = lv.n + 1;
-  const dim3 grid(cdiv(np1, FX), cdiv(np1, FY), zblocks_residual<D>(np1)), block(FX, FY);
+  const GridShape g = resolve(shape, np1);
+  const dim3 grid(cdiv(np1, g.bx), cdiv(np1, g.by), zblocks_residual<D>(np1, g.zr)), block(g.bx, g.by);
   const bool eps = lv.opkind == OP_EPS;
   if (D == 3) {
-    const int zr = residual_zr(np1);
+    const int zr = g.zr;
     if (eps) {
       if (partials) k_residual3g<T, TO, true, true><<<grid, block, 0, s>>>(lv, x, b, r, partials, hD, zr, ctl);
       else k_residual3g<T, TO, true, false><<<grid, block, 0, s>>>(lv, x, b, r, partials, hD, zr, ctl);
@@ -412,9 +422,11 @@ void launch_restrict_g(const LevelView<float>& lf, const LevelView<float>& lc,
 template <int D, bool UPDATE>
 void launch_prolong_g(const LevelView<float>& lf, const LevelView<float>& lc,
                       const CycleParams<float>& cp, const float* r_f, const float* g_f,
-                      const float* t_c, float* x, Control* ctl, cudaStream_t s) {
+                      const float* t_c, float* x, Control* ctl, cudaStream_t s,
+                      GridShape shape) {
   const int np1 = lf.n + 1;
-  const dim3 grid(cdiv(np1, FX), cdiv(np1, FY), D == 3 ? np1 : 1), block(FX, FY);
+  const GridShape g = resolve(shape, np1);
+  const dim3 grid(cdiv(np1, g.bx), cdiv(np1, g.by), D == 3 ? np1 : 1), block(g.bx, g.by);
   const bool pi = cp.variant == V_PI;
   if (lf.boxmg) {
     if (pi) k_prolong_g<D, UPDATE, true, true><<<grid, block, 0, s>>>(lf, lc, cp, r_f, g_f, t_c, x, ctl);
@@ -429,21 +441,21 @@ void launch_prolong_g(const LevelView<float>& lf, const LevelView<float>& lc,
   template int residual_g_blocks<D>(int);                                                      \
   template void launch_residual_g<D, float, float>(const LevelView<float>&, const float*,      \
                                                    const float*, float*, double*, double,      \
-                                                   const Control*, cudaStream_t);              \
+                                                   const Control*, cudaStream_t, GridShape);   \
   template void launch_residual_g<D, double, float>(const LevelView<double>&, const double*,   \
                                                     const double*, float*, double*, double,    \
-                                                    const Control*, cudaStream_t);             \
+                                                    const Control*, cudaStream_t, GridShape);  \
   template void launch_restrict_g<D>(const LevelView<float>&, const LevelView<float>&,         \
                                      const CycleParams<float>&, const float*, float*, float*,  \
                                      float*, float, const Control*, cudaStream_t);             \
   template void launch_prolong_g<D, true>(const LevelView<float>&, const LevelView<float>&,    \
                                           const CycleParams<float>&, const float*,             \
                                           const float*, const float*, float*, Control*,        \
-                                          cudaStream_t);                                       \
+                                          cudaStream_t, GridShape);                            \
   template void launch_prolong_g<D, false>(const LevelView<float>&, const LevelView<float>&,   \
                                            const CycleParams<float>&, const float*,            \
                                            const float*, const float*, float*, Control*,       \
-                                           cudaStream_t);
+                                           cudaStream_t, GridShape);
 
 ADAFAC_LEVEL_INST(2)
 ADAFAC_LEVEL_INST(3)
