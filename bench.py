@@ -120,11 +120,16 @@ def _algorithmic_bytes(kind, w, precision, eps_scalar):
     """Bytes the method must move per launch of a fine-level kernel: the state
     read or written once (interior dofs of the finest level)."""
     N = (3 ** w.depth - 1) ** w.dim
-    eps_b = 0 if eps_scalar else (4 if precision == "mixed" else 8)
-    p_b = (2 ** w.dim) * (4 if precision == "mixed" else 8) if w.transfer == "boxmg" else 0
+    wb = 4 if precision == "mixed" else 8
+    eps_b = 0 if eps_scalar else wb
+    # BoxMG: the weights that are not zero by structure, (1 + 2 + 2)^d per
+    # 3^d fine vertices (a vertex on a coarse plane along an axis takes one
+    # corner there, any other two); d-linear weights are constants
+    p_b = (5.0 / 3.0) ** w.dim * wb if w.transfer == "boxmg" else 0
+    invd_b = 0 if eps_scalar else wb                     # inverse diagonal per vertex
     if precision == "mixed":
         per = {"fine_residual": 4 + 4 + 4 + eps_b,      # e, rhs in; residual out
-               "fine_update": 4 + 4 + 4 + p_b,          # residual, e in; e out
+               "fine_update": 4 + 4 + 4 + p_b + invd_b,  # residual, e in; e out
                "fine_restrict": 4 + p_b,                # residual in
                "refine": 8 + 8 + 4 + 8 * (not eps_scalar),  # u, b in; rhs32 out
                "fine_down": 4 + 4 + 4,                  # e, rhs in; e out
@@ -132,11 +137,11 @@ def _algorithmic_bytes(kind, w, precision, eps_scalar):
                "fine_down_u": 4 + 4 + 8 + 8 + 4}        # e, rhs, u in; u, other e out
     else:
         per = {"fine_residual": 8 + 8 + 8 + eps_b,
-               "fine_update": 8 + 8 + 8 + p_b,
+               "fine_update": 8 + 8 + 8 + p_b + invd_b,
                "fine_restrict": 8 + p_b,
                "refine": 0,
                "fine_down": 0, "fine_up": 0, "fine_down_u": 0}
-    return per[kind] * N
+    return int(round(per[kind] * N))
 
 
 def run_oracle_sample(w, seconds: float):
@@ -310,10 +315,12 @@ def bench_ours(args, w):
     peaks, src = _peaks()
     alg = _algorithmic_bytes(dom, w, args.precision, sc)
     achieved = alg / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
-    traffic = _traffic_from_profile(dom, w, tuning)
+    traffic, capture_shape = _traffic_from_profile(dom, w, tuning)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"] if achieved else None,
                 "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
+                "traffic_launch_shape": capture_shape if traffic and _shape_differs(
+                    capture_shape, tuning) else None,
                 "algorithmic_bytes_per_launch": alg,
                 "avg_launch_us": 1e3 * dom_ms / dom_n if dom_n else None,
                 "share_of_step": dom_ms / max(1e-9, sum(v[0] for v in kt.values())),
@@ -387,14 +394,21 @@ def _e2e(args, w, eps, sc, f, opts, upd_cycle, cycles, adafac, torch, tune):
                         "D2H of u"}
 
 
-def kernel_source_hash():
-    """Fingerprint of the sources of the profiled fine-level kernels (the 3-D
-    sweeps and the refinement residual): DRAM counters taken on another build
-    of them do not describe this one."""
+# Sources of the kernels whose DRAM counters profiles/traffic.json records,
+# per workload: counters taken on another build of them do not describe this one.
+TRAFFIC_SOURCES = {
+    "poisson3d_d5": ("sweep3.cu", "sweep3.cuh", "common.cuh", "mbarrier.cuh"),
+    "jump3d_d5": ("level.cu", "common.cuh"),
+}
+
+
+def kernel_source_hash(files=("sweep3.cu", "sweep3.cuh", "common.cuh", "mbarrier.cuh")):
+    """Fingerprint of the sources of profiled fine-level kernels (by default
+    the 3-D sweeps and the refinement residual)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1903_10367_gb300", "csrc")
     h = hashlib.sha256()
-    for name in ("sweep3.cu", "sweep3.cuh", "common.cuh", "mbarrier.cuh"):
+    for name in files:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -483,24 +497,30 @@ def run_serving(count: int, seed: int = 1903):
     }
 
 
-def _traffic_from_profile(kind, w, tuning=None):
+def _traffic_from_profile(kind, w, tuning=None, table=None):
     """DRAM bytes (read + write) per launch of this kernel from the committed
-    ncu summary (profiles/traffic.json), or None when the summary was taken on
-    other kernel sources or with other tile depths of the sweeps."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    ncu summary (profiles/traffic.json) and the launch shape of that capture,
+    or (None, None) when the summary was taken on other kernel sources or
+    holds no figure for the kernel."""
     try:
-        with open(path) as fh:
-            table = json.load(fh)
-        if table.get("source_hash") != kernel_source_hash():
-            return None
-        entry = table.get(w.name, {})
-        if tuning and tuning.get("path") == 1 and "sweep_zc" in entry:
-            if (entry["sweep_zc"], entry["sweep_zc_down"]) != (tuning["sweep_zc"],
-                                                               tuning["sweep_zc_down"]):
-                return None
-        return entry.get(kind)
+        if table is None:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+                table = json.load(fh)
+        entry = table.get(w.name)
+        files = TRAFFIC_SOURCES.get(w.name)
+        if not entry or not files or entry.get("source_hash") != kernel_source_hash(files):
+            return None, None
+        return entry.get("bytes", {}).get(kind), entry.get("launch_shape")
     except Exception:
-        return None
+        return None, None
+
+
+def _shape_differs(capture_shape, tuning):
+    """True when the traffic capture ran other launch shapes than the timed run."""
+    if not capture_shape:
+        return False
+    run = {k: (tuning or {}).get(k) for k in capture_shape}
+    return run != capture_shape
 
 
 def main():

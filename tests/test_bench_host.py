@@ -32,3 +32,36 @@ def test_l2_flush_only_for_small_workloads():
 def test_kernel_fingerprint_is_stable():
     assert bench.kernel_source_hash() == bench.kernel_source_hash()
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_algorithmic_bytes_of_the_level_kernels_count_structural_nonzeros():
+    # BoxMG weights that are not zero by structure: (5/3)^3 per fine vertex
+    w = wl.get("jump3d_d5")
+    N = 242 ** 3
+    p_b = (5.0 / 3.0) ** 3 * 4
+    assert bench._algorithmic_bytes("fine_update", w, "mixed", False) == round((12 + p_b + 4) * N)
+    assert bench._algorithmic_bytes("fine_restrict", w, "mixed", False) == round((4 + p_b) * N)
+    assert bench._algorithmic_bytes("fine_residual", w, "mixed", False) == 16 * N
+
+
+def test_traffic_lookup_checks_sources_and_reports_the_capture_shape():
+    w = wl.get("poisson3d_d5")
+    good = bench.kernel_source_hash(bench.TRAFFIC_SOURCES["poisson3d_d5"])
+    table = {"poisson3d_d5": {"source_hash": good, "launch_shape": {"sweep_zc": 9, "sweep_zc_down": 9},
+                              "bytes": {"fine_up": 123}}}
+    assert bench._traffic_from_profile("fine_up", w, table=table) == (123, {"sweep_zc": 9, "sweep_zc_down": 9})
+    assert bench._traffic_from_profile("fine_down", w, table=table)[0] is None
+    stale = {"poisson3d_d5": dict(table["poisson3d_d5"], source_hash="0" * 16)}
+    assert bench._traffic_from_profile("fine_up", w, table=stale) == (None, None)
+    assert bench._shape_differs({"sweep_zc": 9, "sweep_zc_down": 9}, {"sweep_zc": 8, "sweep_zc_down": 8})
+    assert not bench._shape_differs({"sweep_zc": 9, "sweep_zc_down": 9}, {"sweep_zc": 9, "sweep_zc_down": 9, "path": 1})
+    assert not bench._shape_differs(None, {"sweep_zc": 8})
+
+
+def test_committed_traffic_table_matches_the_current_kernel_sources():
+    # the committed ncu figures describe the kernels in this tree
+    for name in ("poisson3d_d5", "jump3d_d5"):
+        w = wl.get(name)
+        kinds = {"poisson3d_d5": "fine_up", "jump3d_d5": "fine_restrict"}
+        traffic, _ = bench._traffic_from_profile(kinds[name], w)
+        assert traffic and traffic > 0, name

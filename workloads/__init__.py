@@ -161,6 +161,11 @@ WORKLOADS = {
                           block_cells=27, seed=1903, rhs_kind="constant",
                           transfer="boxmg"),
     "poisson3d_d5": Workload("poisson3d_d5", 3, 5, "scalar"),
+    # the largest request of the serving mix: 3-D depth 5, eps on blocks of
+    # level-3 cells (9^3 fine cells), each 1 or 1e-2; f = 1; BoxMG + Galerkin
+    "jump3d_d5": Workload("jump3d_d5", 3, 5, "blocks", eps_low=1e-2,
+                          block_cells=9, seed=1903, rhs_kind="constant",
+                          transfer="boxmg"),
 }
 
 
