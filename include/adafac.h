@@ -51,7 +51,8 @@ typedef enum {
 } adafac_status;
 
 /* Regular spacetree: dim in {2, 3}, 1 <= depth (L), ((3^L+1)^dim must fit in
- * 2^31 vertices).  l_min is fixed to 1 (the paper's benchmark setting,
+ * 2^31 vertices).  The coarsest level taking part in the cycles is
+ * adafac_options.lmin (1 by default, the paper's benchmark setting,
  * Sec. 2.1). */
 typedef struct {
   int dim;

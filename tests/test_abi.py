@@ -103,3 +103,53 @@ def test_server_arguments_are_checked_before_any_device_call():
     assert lib.adafac_poll(None, 1, ctypes.byref(info)) == 1
     assert lib.adafac_fetch(None, 1, None) == 1
     assert lib.adafac_server_destroy(None) == 1
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled
+    against include/adafac.h with the host compiler."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    body = "\n".join(f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src = f"""#include <stddef.h>
+#include <stdio.h>
+#include "adafac.h"
+int main(void) {{
+  printf("%zu\\n", sizeof({struct}));
+{body}
+  return 0;
+}}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+@pytest.mark.parametrize("struct,cls", [("adafac_tree", adafac.Tree),
+                                        ("adafac_options", adafac.Options),
+                                        ("adafac_tuning", adafac.Tuning),
+                                        ("adafac_request_info", adafac.RequestInfo)])
+def test_binding_structs_match_the_header_layout(struct, cls):
+    names = [n for n, _ in cls._fields_]
+    got = _c_layout(struct, names)
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, n).offset for n in names]
+
+
+def test_autotune_and_path_arguments_are_checked_on_the_host():
+    lib = adafac.load()
+    t = adafac.Tuning()
+    assert lib.adafac_autotune(None, 5, ctypes.byref(t)) == 1
+    assert adafac.workspace_size(3, 3, adafac.default_options(precision="mixed", path="generic")) > 0
+    bad = adafac.default_options()
+    bad.path = 3
+    with pytest.raises(adafac.AdafacError):
+        adafac.workspace_size(2, 3, bad)
