@@ -232,6 +232,23 @@ def _config(w, args, cycles):
             "parallelism": f"replicas x{args.gpus}"}
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values: the job takes as long as its slowest
+    replica.  dist None (one process) returns value."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, cycles, updates_per_cycle, ms):
+    """Vertex updates per second of the whole job: every rank solves its own
+    replica (steps solves of `cycles` cycles each) within ms milliseconds."""
+    return world * steps * cycles * updates_per_cycle / (ms / 1e3)
+
+
 def bench_ours(args, w):
     import torch
     world, rank, local = _dist()
@@ -297,11 +314,8 @@ def bench_ours(args, w):
     rel_final = S.residual_norm()[0]
     if not rel_final <= args.tol * 1.0000001:
         raise RuntimeError(f"solve did not reach the tolerance: {rel_final}")
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * cycles * upd_cycle / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(world, args.steps, cycles, upd_cycle, ms)
     # roofline: per-kernel CUDA-event timing over a second timed region
     S.timing(True)
     for _ in range(args.steps):
