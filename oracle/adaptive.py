@@ -1,0 +1,409 @@
+"""The additive cycles on an adaptive 3:1 spacetree (regular or ragged levels).
+
+Oracle (test infrastructure only).  Follows Sec. 2.1 of the paper: cells of
+level l are cut into 3^d children where the tree refines; a vertex of level l
+that is surrounded by 2^d cells of its level carries a d-linear pagoda, the
+others are hanging (or boundary) vertices and carry no test function.  The
+shape functions of all levels form a hierarchical generating system over the
+adaptive grid; the nodal space over the adaptive grid (the composite space
+V_h) consists of the functions that are continuous and d-linear on every leaf
+cell, and the pagoda of every level's active vertex lies in it.
+
+Every function is held by its values at the leaf nodes (all corners of leaf
+cells, hanging positions included), so
+  * the bilinear form is the sum of the leaf cells' element matrices,
+    a(u, v) = v^T K u (Sec. 2.1: eps_c h^(d-2) K_ref per cell);
+  * the load is lumped per leaf cell (the reading of the regular oracle:
+    every corner of a cell of width h takes h^d / 2^d f(x));
+  * the level-l pagodas are the columns of Phi_l (their values at the leaf
+    nodes), and the residual that level l sees is r_l = Phi_l^T (b - K u),
+    the residual of the composite problem tested with level l's shape
+    functions.  This is what the FAS/HTMG right-hand sides of Eq. 4 deliver
+    with Galerkin operators; on a fully refined tree Phi_l = P^(L-l) and
+    r_l = R^(L-l) r_L (Alg. 1).
+The level operator of level l is A_l = Phi_l^T K Phi_l (Ritz-Galerkin over
+the generating system, Sec. 2.2) and M_l = diag(A_l).
+
+The cycle is Eq. 9 on the generating system: every level takes a damped
+Jacobi step on its residual, the damping equation of level l-1 takes the
+smoothed restriction of level l's residual (Eq. 8), and
+  u += sum_l Phi_l c_l - sum_{l >= 2} Phi_{l-1} c~_{l-1}.
+
+Readings for the adaptive tree (the paper leaves them open):
+  * the smoothed restriction's window on level l covers only the level's
+    active vertices: residuals at hanging or absent positions count as zero;
+  * the exact R~ of level l is omega Phi_{l-1}^T K Phi_l M_l^-1 r_l (R A_l
+    with A_l and R taken over the generating system);
+  * eps of a leaf cell coarser than the given fine eps is the mean of the
+    fine cells it covers;
+  * the residual norm of Eq. 10 runs over the vertices of the nodal space
+    (every free position once, on the finest level where it is active), with
+    h_i the spacing of that level.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import cycle as rc
+from .fem import corners, reference_element_matrix
+
+OMEGA = rc.OMEGA
+OMEGA_TILDE = rc.OMEGA_TILDE
+
+
+# --------------------------------------------------------------------------
+# the tree
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class AdaptiveTree:
+    """Spacetree of depth L: exists[l] marks the level-l cells that exist,
+    refined[l] those that are cut into 3^d children (none on level L).  Level
+    1 always exists in full (l_min = 1)."""
+    d: int
+    L: int
+    exists: dict
+    refined: dict
+
+    @property
+    def N(self) -> int:
+        return 3 ** self.L
+
+
+def tree_from_refinement(d: int, L: int, refine) -> AdaptiveTree:
+    """Builds a tree top-down: refine(l, centres, h) -> bool array tells, for
+    the existing level-l cells with the given centres (shape (..., d), last
+    axis = x), which are cut (l < L)."""
+    exists, refined = {}, {}
+    exists[1] = np.ones((3,) * d, dtype=bool)
+    for l in range(1, L + 1):
+        n = 3 ** l
+        h = 1.0 / n
+        if l == L:
+            refined[l] = np.zeros((n,) * d, dtype=bool)
+            break
+        idx = np.indices((n,) * d)
+        # centres with the last array axis as the x coordinate
+        centres = np.stack([(idx[d - 1 - k] + 0.5) * h for k in range(d)], axis=-1)
+        want = np.asarray(refine(l, centres, h), dtype=bool)
+        refined[l] = exists[l] & want
+        child = refined[l]
+        for ax in range(d):
+            child = np.repeat(child, 3, axis=ax)
+        exists[l + 1] = child
+    return AdaptiveTree(d, L, exists, refined)
+
+
+def regular_tree(d: int, L: int) -> AdaptiveTree:
+    return tree_from_refinement(d, L, lambda l, c, h: np.ones(c.shape[:-1], dtype=bool))
+
+
+# --------------------------------------------------------------------------
+# the discrete system over the leaf nodes
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class AdaptiveSystem:
+    tree: AdaptiveTree
+    node_id: np.ndarray     # (N+1)^d: leaf node id at every fine-index position, -1 if none
+    coords: np.ndarray      # (n_nodes, d) fine indices of the leaf nodes (array-axis order)
+    boundary: np.ndarray    # (n_nodes,) bool
+    K: sp.csr_matrix        # leaf stiffness
+    b: np.ndarray           # lumped load at the leaf nodes
+    Phi: dict               # l -> (n_nodes, n_active_l) pagodas of level l's active vertices
+    PhiB: dict              # l -> (n_nodes, n_b) truncated pagodas of level l's boundary vertices
+    bnd: dict               # l -> (n_b, d) those boundary vertices (level-l indices)
+    active: dict            # l -> (n_active_l, d) level-l vertex indices of the active vertices
+    active_grid: dict       # l -> (3^l+1)^d int: column of Phi_l, -1 if not active
+    diag: dict              # l -> diag(Phi_l^T K Phi_l)
+    S_trunc: np.ndarray     # truncated smoothed restriction stencil (5^d)
+
+    @property
+    def d(self) -> int:
+        return self.tree.d
+
+    @property
+    def L(self) -> int:
+        return self.tree.L
+
+
+def _leaf_cells(tree: AdaptiveTree):
+    """(level, cell index array (m, d)) of every leaf cell."""
+    out = []
+    for l in range(1, tree.L + 1):
+        leaf = tree.exists[l] & ~tree.refined[l]
+        out.append((l, np.argwhere(leaf)))
+    return out
+
+
+def _leaf_eps(eps, tree: AdaptiveTree, l: int, cells: np.ndarray) -> np.ndarray:
+    if np.ndim(eps) == 0 or np.size(eps) == 1:
+        return np.full(len(cells), float(np.ravel(eps)[0]))
+    s = 3 ** (tree.L - l)
+    out = np.empty(len(cells))
+    for i, c in enumerate(cells):
+        sl = tuple(slice(s * ck, s * ck + s) for ck in c)
+        out[i] = eps[sl].mean()
+    return out
+
+
+def build_system(tree: AdaptiveTree, eps, f) -> AdaptiveSystem:
+    """Leaf nodes, leaf stiffness and load, and every level's pagodas.
+
+    eps: scalar or per fine cell (shape (N,)*d); f: values at the fine-index
+    positions (shape (N+1,)*d)."""
+    d, L, N = tree.d, tree.L, tree.N
+    cs = np.array(corners(d))                      # corner offsets, array-axis order
+    Kref = reference_element_matrix(d)
+    leaves = _leaf_cells(tree)
+    # leaf nodes
+    present = np.zeros((N + 1,) * d, dtype=bool)
+    for l, cells in leaves:
+        s = 3 ** (L - l)
+        for b in cs:
+            pos = s * (cells + b)
+            present[tuple(pos.T)] = True
+    node_id = -np.ones((N + 1,) * d, dtype=np.int64)
+    coords = np.argwhere(present)
+    node_id[tuple(coords.T)] = np.arange(len(coords))
+    boundary = np.any((coords == 0) | (coords == N), axis=1)
+    # stiffness and lumped load
+    rows, cols, vals = [], [], []
+    b = np.zeros(len(coords))
+    for l, cells in leaves:
+        if len(cells) == 0:
+            continue
+        s = 3 ** (L - l)
+        h = 1.0 / 3 ** l
+        e = _leaf_eps(eps, tree, l, cells)
+        ids = np.stack([node_id[tuple((s * (cells + bb)).T)] for bb in cs], axis=1)
+        scale = e * h ** (d - 2)
+        for a in range(len(cs)):
+            for bb in range(len(cs)):
+                rows.append(ids[:, a])
+                cols.append(ids[:, bb])
+                vals.append(scale * Kref[a, bb])
+            np.add.at(b, ids[:, a], (h ** d / 2 ** d) * f[tuple(coords[ids[:, a]].T)])
+    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(len(coords),) * 2)
+    # active vertices and their pagodas at the leaf nodes
+    Phi, active, active_grid, diag, PhiB, bnd = {}, {}, {}, {}, {}, {}
+
+    def pagodas(verts, s):
+        # values of the pagodas of width s (fine units) at the leaf nodes,
+        # truncated to the domain
+        r_, c_, v_ = [], [], []
+        for off in itertools.product(range(-s + 1, s), repeat=d):
+            w = np.prod([1.0 - abs(o) / s for o in off])
+            pos = s * verts + np.array(off)
+            inside = np.all((pos >= 0) & (pos <= N), axis=1)
+            ids = -np.ones(len(verts), dtype=np.int64)
+            ids[inside] = node_id[tuple(pos[inside].T)]
+            ok = ids >= 0
+            r_.append(ids[ok])
+            c_.append(np.nonzero(ok)[0])
+            v_.append(np.full(int(ok.sum()), w))
+        return sp.csr_matrix((np.concatenate(v_), (np.concatenate(r_), np.concatenate(c_))),
+                             shape=(len(coords), len(verts)))
+
+    for l in range(1, L + 1):
+        n = 3 ** l
+        s = 3 ** (L - l)
+        # vertex j is surrounded by the cells j - 1 + b, b in {0,1}^d; cells
+        # outside the domain count as present for boundary vertices
+        pad = np.zeros((n + 2,) * d, dtype=bool)
+        pad[tuple(slice(1, n + 1) for _ in range(d))] = tree.exists[l]
+        padb = np.ones((n + 2,) * d, dtype=bool)
+        padb[tuple(slice(1, n + 1) for _ in range(d))] = tree.exists[l]
+        surrounded = np.ones((n + 1,) * d, dtype=bool)
+        surrounded_b = np.ones((n + 1,) * d, dtype=bool)
+        for bb in cs:
+            sl = tuple(slice(bk, bk + n + 1) for bk in bb)
+            surrounded &= pad[sl]
+            surrounded_b &= padb[sl]
+        inner = np.zeros((n + 1,) * d, dtype=bool)
+        inner[tuple(slice(1, n) for _ in range(d))] = True
+        act = np.argwhere(surrounded & inner)
+        grid = -np.ones((n + 1,) * d, dtype=np.int64)
+        grid[tuple(act.T)] = np.arange(len(act))
+        Ph = pagodas(act, s)
+        Phi[l], active[l], active_grid[l] = Ph, act, grid
+        diag[l] = np.asarray((Ph.multiply(K @ Ph)).sum(axis=0)).ravel()
+        bv = np.argwhere(surrounded_b & ~inner)
+        PhiB[l], bnd[l] = pagodas(bv, s), bv
+    S = rc.truncate_stencil(rc.smoothed_prolongation_stencil(d))
+    return AdaptiveSystem(tree, node_id, coords, boundary, K, b, Phi, PhiB, bnd, active,
+                          active_grid, diag, S)
+
+
+# --------------------------------------------------------------------------
+# residuals, the composite problem, the cycle
+# --------------------------------------------------------------------------
+
+def free_vertices(sys_: AdaptiveSystem):
+    """The vertices of the nodal space over the adaptive grid: every position
+    that is an active vertex of some level, on the finest such level.
+    Returns (levels, columns): level l and column of Phi_l of each."""
+    finest = -np.ones(len(sys_.coords), dtype=np.int64)
+    col = -np.ones(len(sys_.coords), dtype=np.int64)
+    for l in range(1, sys_.L + 1):
+        s = 3 ** (sys_.L - l)
+        ids = sys_.node_id[tuple((s * sys_.active[l]).T)]
+        finest[ids] = l
+        col[ids] = np.arange(len(ids))
+    sel = np.nonzero(finest >= 0)[0]
+    return finest[sel], col[sel], sel
+
+
+def composite_basis(sys_: AdaptiveSystem) -> sp.csr_matrix:
+    """Columns: the pagoda of every free position on its finest level."""
+    lev, col, _ = free_vertices(sys_)
+    blocks = [sys_.Phi[l][:, col[lev == l]] for l in range(1, sys_.L + 1) if np.any(lev == l)]
+    return sp.hstack(blocks).tocsr()
+
+
+def residual(sys_: AdaptiveSystem, u: np.ndarray) -> np.ndarray:
+    """b - K u at the leaf nodes (Dirichlet nodes included; nothing tests them)."""
+    return sys_.b - sys_.K @ u
+
+
+def level_residuals(sys_: AdaptiveSystem, u: np.ndarray, lmin: int = 1) -> dict:
+    rr = residual(sys_, u)
+    return {l: sys_.Phi[l].T @ rr for l in range(lmin, sys_.L + 1)}
+
+
+def residual_norm(sys_: AdaptiveSystem, u: np.ndarray) -> float:
+    """Eq. 10 over the vertices of the nodal space, h_i of their level."""
+    rr = residual(sys_, u)
+    lev, col, _ = free_vertices(sys_)
+    acc = 0.0
+    for l in range(1, sys_.L + 1):
+        m = lev == l
+        if not np.any(m):
+            continue
+        r_l = sys_.Phi[l].T @ rr
+        acc += float(np.sum((3.0 ** -l) ** sys_.d * r_l[col[m]] ** 2))
+    return float(np.sqrt(acc))
+
+
+def _to_grid(sys_: AdaptiveSystem, l: int, x: np.ndarray) -> np.ndarray:
+    g = np.zeros((3 ** l + 1,) * sys_.d)
+    g[tuple(sys_.active[l].T)] = x
+    return g
+
+
+def smoothed_restriction(sys_: AdaptiveSystem, l: int, r_l: np.ndarray, omega: float,
+                         mode: str = "truncated") -> np.ndarray:
+    """b~_{l-1} on the active vertices of level l-1 (Eq. 8)."""
+    if mode == "truncated":
+        g = rc.apply_stencil_at_coarse(sys_.S_trunc, _to_grid(sys_, l, r_l))
+        return omega * g[tuple(sys_.active[l - 1].T)]
+    if mode == "exact":
+        y = sys_.K @ (sys_.Phi[l] @ (r_l / sys_.diag[l]))
+        return omega * (sys_.Phi[l - 1].T @ y)
+    raise ValueError(mode)
+
+
+def inject(sys_: AdaptiveSystem, l: int, x_l: np.ndarray) -> np.ndarray:
+    """I: values of level l at the active vertices of level l-1 (the level-l
+    vertex at the same position; zero where it is not active)."""
+    g = _to_grid(sys_, l, x_l)
+    return g[tuple((3 * sys_.active[l - 1]).T)]
+
+
+def cycle(sys_: AdaptiveSystem, u: np.ndarray, variant: str = "jac", rtilde: str = "truncated",
+          omega: float = OMEGA, omega_tilde: float = OMEGA_TILDE, omega_exp: float = 0.5,
+          lmin: int = 1, return_parts: bool = False):
+    """One additive cycle (Eq. 9 on the generating system) over levels lmin..L.
+
+    jac: u += sum_l Phi_l c_l - sum_{l>lmin} Phi_{l-1} c~_{l-1}, c~_{l-1} =
+         omega~ M_{l-1}^-1 R~ r_l;  pi: c~ of level l is P I c_l, so
+         u += sum_l Phi_l c_l - sum_{l>lmin} Phi_{l-1} I c_l;  additive / exp:
+         Eq. 2 with omega_add = 1 / omega_exp^(L-l) (the global depth L)."""
+    L = sys_.L
+    r = level_residuals(sys_, u, lmin)
+    c = {l: omega * r[l] / sys_.diag[l] for l in range(lmin, L + 1)}
+    du = np.zeros_like(u)
+    for l in range(lmin, L + 1):
+        scale = omega_exp ** (L - l) if variant == "exp" else 1.0
+        du += scale * (sys_.Phi[l] @ c[l])
+    parts = {"r": r, "c": c}
+    if variant == "jac":
+        bt, ct = {}, {}
+        for l in range(lmin + 1, L + 1):
+            bt[l - 1] = smoothed_restriction(sys_, l, r[l], omega, rtilde)
+            ct[l - 1] = omega_tilde * bt[l - 1] / sys_.diag[l - 1]
+            du -= sys_.Phi[l - 1] @ ct[l - 1]
+        parts["bt"], parts["ct"] = bt, ct
+    elif variant == "pi":
+        for l in range(lmin + 1, L + 1):
+            du -= sys_.Phi[l - 1] @ inject(sys_, l, c[l])
+    elif variant not in ("additive", "exp"):
+        raise ValueError(variant)
+    u_new = u + du
+    if return_parts:
+        return u_new, parts
+    return u_new
+
+
+def solve(sys_: AdaptiveSystem, u0=None, tol: float = 1e-8, max_cycles: int = 2000, **kw):
+    """Cycles until ||r||_h / ||r_0||_h <= tol (Eq. 10); returns (u, history)."""
+    u = np.zeros(len(sys_.coords)) if u0 is None else u0.copy()
+    r0 = residual_norm(sys_, u)
+    hist = [1.0]
+    for _ in range(max_cycles):
+        u = cycle(sys_, u, **kw)
+        rel = residual_norm(sys_, u) / r0 if r0 > 0 else 0.0
+        hist.append(rel)
+        if not np.isfinite(rel) or rel > 1e6 or rel <= tol:
+            break
+    return u, np.array(hist)
+
+
+def dirichlet_lift(sys_: AdaptiveSystem, g: np.ndarray) -> np.ndarray:
+    """A function of the adaptive grid's space (continuous, d-linear on every
+    leaf cell) that takes the Dirichlet values g at the boundary vertices:
+    a combination of the truncated pagodas of the boundary vertices, each
+    position on the finest level where it is a boundary vertex surrounded by
+    its level's cells.  Boundary nodes that hang take the interpolated value
+    (g there is not used)."""
+    finest = {}
+    for l in range(1, sys_.L + 1):
+        s = 3 ** (sys_.L - l)
+        for k, v in enumerate(sys_.bnd[l]):
+            finest[tuple(s * v)] = (l, k)
+    # the pagodas are hierarchical, not nodal: a coarse one is non-zero at
+    # finer positions, a fine one vanishes at every coarser position.  So the
+    # positions are set from the coarsest level down, each with the part of
+    # g the coarser pagodas have not produced there yet.
+    u = np.zeros(len(sys_.coords))
+    for lev in range(1, sys_.L + 1):
+        for pos, (l, k) in finest.items():
+            if l != lev:
+                continue
+            i = sys_.node_id[pos]
+            u += (g[i] - u[i]) * sys_.PhiB[l][:, k].toarray().ravel()
+    return u
+
+
+def direct_solution(sys_: AdaptiveSystem, g=None) -> np.ndarray:
+    """The solution of the composite problem: find u in V_h (with Dirichlet
+    values g at the boundary vertices, zero if None) such that a(u, phi) =
+    (f, phi) for every basis function phi of the nodal space."""
+    B = composite_basis(sys_)
+    uD = np.zeros(len(sys_.coords)) if g is None else dirichlet_lift(sys_, g)
+    rhs = B.T @ (sys_.b - sys_.K @ uD)
+    A = (B.T @ sys_.K @ B).tocsc()
+    x = spla.spsolve(A, rhs)
+    return uD + B @ x
+
+
+def sample(sys_: AdaptiveSystem, fn) -> np.ndarray:
+    """fn(x) at the leaf nodes; x has the last array axis as the x coordinate."""
+    pts = sys_.coords[:, ::-1] / sys_.tree.N
+    return fn(pts)

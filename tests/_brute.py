@@ -71,3 +71,63 @@ def dlinear_prolongation_dense(d: int, n_c: int) -> np.ndarray:
 
 def interior_block(M: np.ndarray, rows_mask, cols_mask) -> np.ndarray:
     return M[np.ix_(rows_mask, cols_mask)]
+
+
+# ---------------------------------------------------------------------------
+# adaptive trees: the nodal space over the leaf cells, from the global hats
+
+def leaf_cells(tree):
+    """(level, cell index tuple) of every leaf cell of a tree given by its
+    per-level ``exists`` / ``refined`` flags."""
+    out = []
+    for l in range(1, tree.L + 1):
+        leaf = tree.exists[l] & ~tree.refined[l]
+        out += [(l, tuple(c)) for c in np.argwhere(leaf)]
+    return out
+
+
+def hats_and_grads(pos: np.ndarray, widths: np.ndarray, x: np.ndarray):
+    """Values and gradients at x of the hats centred at pos (rows) with the
+    given widths (one per row)."""
+    t = (x[None, :] - pos) / widths[:, None]
+    psi = np.maximum(0.0, 1.0 - np.abs(t))
+    dpsi = np.where(np.abs(t) < 1.0, -np.sign(t), 0.0) / widths[:, None]
+    d = pos.shape[1]
+    grad = np.empty_like(pos)
+    for k in range(d):
+        others = np.prod(np.delete(psi, k, axis=1), axis=1) if d > 1 else 1.0
+        grad[:, k] = dpsi[:, k] * others
+    return np.prod(psi, axis=1), grad
+
+
+def adaptive_system_dense(tree, eps_fine, f_fn, pos: np.ndarray, widths: np.ndarray):
+    """A[i, j] = sum over leaf cells c of eps_c int_c grad phi_i . grad phi_j and
+    the lumped load b_i = sum_c |c| / 2^d sum_{corners x} f(x) phi_i(x), for the
+    hats phi_i of the given positions and widths (positions in [0,1]^d, array
+    axis order).  eps of a leaf cell: the mean of the fine cells it covers.
+    2-point Gauss per direction is exact: every hat is d-linear on every leaf
+    cell."""
+    d = tree.d
+    g, w = np.polynomial.legendre.leggauss(2)
+    g = 0.5 * (g + 1.0)
+    w = 0.5 * w
+    A = np.zeros((len(pos), len(pos)))
+    b = np.zeros(len(pos))
+    for l, cell in leaf_cells(tree):
+        h = 1.0 / 3 ** l
+        s = 3 ** (tree.L - l)
+        e = float(np.mean(eps_fine[tuple(slice(s * c, s * c + s) for c in cell)])) \
+            if np.ndim(eps_fine) else float(eps_fine)
+        lo = np.array(cell) * h
+        for q in itertools.product(range(2), repeat=d):
+            x = lo + np.array([g[k] for k in q]) * h
+            wq = np.prod([w[k] for k in q]) * h ** d
+            _, grad = hats_and_grads(pos, widths, x)
+            nz = np.nonzero(np.any(grad != 0.0, axis=1))[0]
+            G = grad[nz]
+            A[np.ix_(nz, nz)] += e * wq * (G @ G.T)
+        for corner in itertools.product((0, 1), repeat=d):
+            x = lo + np.array(corner) * h
+            val, _ = hats_and_grads(pos, widths, x)
+            b += (h ** d / 2 ** d) * f_fn(x) * val
+    return A, b

@@ -1,0 +1,132 @@
+"""Pins of the adaptive-tree oracle (oracle/adaptive.py).
+
+* On a fully refined tree the generating-system cycle is the regular
+  oracle's cycle, for every variant and both smoothed restrictions.
+* On adaptive trees with hanging vertices, the composite problem it solves
+  equals the one assembled from the global hat functions by quadrature over
+  the leaf cells (tests/_brute.py), and the cycles converge to its solution.
+* Linear boundary data with f = 0 give the linear function at every leaf
+  node, hanging ones included: the space reproduces linears.
+* Iterates stay in the space of the adaptive grid: values at hanging nodes
+  are the interpolation of the surrounding vertices.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import adaptive as ad
+from oracle import cycle as oc
+
+from . import _brute
+
+
+def _band_tree(d, L):
+    # refine a band around the circle r = 0.3 about the centre (the shape of
+    # the adaptive workload), coarser far from it
+    def ref(l, c, h):
+        r = np.sqrt(((c - 0.5) ** 2).sum(-1))
+        return np.abs(r - 0.3) <= 0.05 + h
+    return ad.tree_from_refinement(d, L, ref)
+
+
+def _corner_tree(d, L):
+    return ad.tree_from_refinement(d, L, lambda l, c, h: np.all(c < 0.4, axis=-1))
+
+
+@pytest.mark.parametrize("d,L", [(2, 3), (3, 2)])
+@pytest.mark.parametrize("variant,rtilde", [("jac", "truncated"), ("jac", "exact"),
+                                            ("additive", "truncated"), ("pi", "truncated"),
+                                            ("exp", "truncated")])
+def test_fully_refined_tree_is_the_regular_cycle(d, L, variant, rtilde):
+    N = 3 ** L
+    eps = np.random.default_rng(5).uniform(0.05, 2.0, size=(N,) * d)
+    f = wl.manufactured_rhs(d, L)
+    S = ad.build_system(ad.regular_tree(d, L), eps, f)
+    H = oc.build_hierarchy(d, L, eps, False, f, "dlinear")
+    u0g = wl.random_vertex_field(d, L, 11)
+    u0 = u0g[tuple(S.coords.T)]
+    ua = ad.cycle(S, u0, variant=variant, rtilde=rtilde, omega_exp=0.7)
+    ur = oc.cycle(H, u0g, variant=variant, rtilde=rtilde, omega_exp=0.7)
+    assert np.abs(ua - ur[tuple(S.coords.T)]).max() <= 1e-13 * np.abs(ur).max()
+    assert ad.residual_norm(S, u0) == pytest.approx(
+        oc.residual_norm(H, oc.residual(H, L, u0g, H.b)), rel=1e-13)
+
+
+def _active_vertices_by_hand(T):
+    """Every level's vertices surrounded by 2^d existing cells of their level
+    (interior ones), found vertex by vertex from the tree's flags."""
+    d = T.d
+    out = []
+    for l in range(1, T.L + 1):
+        n = 3 ** l
+        for v in itertools.product(range(1, n), repeat=d):
+            if all(T.exists[l][tuple(vk - 1 + bk for vk, bk in zip(v, b))]
+                   for b in itertools.product((0, 1), repeat=d)):
+                out.append((l, v))
+    return out
+
+
+@pytest.mark.parametrize("tree", ["corner", "band"])
+def test_composite_problem_equals_the_hat_function_assembly(tree):
+    # second route: all shape functions of the generating system (every
+    # level's active vertices, found by hand), global hats, quadrature on the
+    # leaf cells, a least-squares solve of the singular system; its function
+    # must equal the oracle's solution at every leaf node, hanging ones too
+    d, L = 2, 3
+    T = _corner_tree(d, L) if tree == "corner" else _band_tree(d, L)
+    N = 3 ** L
+    eps = np.random.default_rng(3).uniform(0.2, 3.0, size=(N,) * d)
+    f = wl.manufactured_rhs(d, L)
+    S = ad.build_system(T, eps, f)
+    u = ad.direct_solution(S)
+    gen = _active_vertices_by_hand(T)
+    pos = np.array([np.array(v) / 3 ** l for l, v in gen])
+    widths = np.array([3.0 ** -l for l, _ in gen])
+    f_fn = lambda x: f[tuple(np.rint(x * N).astype(int))]
+    A, b = _brute.adaptive_system_dense(T, eps, f_fn, pos, widths)
+    x, *_ = np.linalg.lstsq(A, b, rcond=1e-13)
+    vals = np.array([_brute.hats_and_grads(pos, widths, p / N)[0] @ x for p in S.coords])
+    assert np.abs(u - vals).max() <= 1e-9 * np.abs(vals).max()
+    lev, col, sel = ad.free_vertices(S)
+    assert len(sel) < len(S.coords) - S.boundary.sum()  # the tree has hanging nodes
+
+
+@pytest.mark.parametrize("d,L,tree", [(2, 4, "band"), (2, 3, "corner"), (3, 3, "corner")])
+@pytest.mark.parametrize("variant", ["jac", "additive", "pi"])
+def test_cycles_converge_to_the_composite_solution(d, L, tree, variant):
+    T = _corner_tree(d, L) if tree == "corner" else _band_tree(d, L)
+    S = ad.build_system(T, 1.0, wl.constant_rhs(d, L))
+    ud = ad.direct_solution(S)
+    u, hist = ad.solve(S, tol=1e-11, max_cycles=1000, variant=variant)
+    assert hist[-1] <= 1e-11
+    assert np.abs(u - ud).max() <= 1e-8 * np.abs(ud).max()
+
+
+@pytest.mark.parametrize("tree", ["corner", "band"])
+def test_linear_boundary_data_give_the_linear_solution(tree):
+    d, L = 2, 4
+    T = _corner_tree(d, L) if tree == "corner" else _band_tree(d, L)
+    S = ad.build_system(T, 1.0, np.zeros((3 ** L + 1,) * d))
+    g = ad.sample(S, lambda x: 1.0 + 2.0 * x[:, 0] - 3.0 * x[:, 1])
+    assert np.abs(ad.dirichlet_lift(S, g) - g)[S.boundary].max() <= 1e-14
+    assert np.abs(ad.direct_solution(S, g) - g).max() <= 1e-12
+    u, hist = ad.solve(S, u0=ad.dirichlet_lift(S, g), tol=1e-12, max_cycles=1000)
+    assert np.abs(u - g).max() <= 1e-10
+
+
+def test_iterates_stay_in_the_space_of_the_adaptive_grid():
+    d, L = 2, 3
+    S = ad.build_system(_corner_tree(d, L), 1.0, wl.manufactured_rhs(d, L))
+    B = ad.composite_basis(S).toarray()
+    u = B @ np.random.default_rng(1).standard_normal(B.shape[1])
+    for _ in range(3):
+        u = ad.cycle(S, u)
+    # u is a combination of the nodal space's basis functions: hanging nodes
+    # carry the interpolated values
+    x, *_ = np.linalg.lstsq(B, u, rcond=None)
+    assert np.abs(B @ x - u).max() <= 1e-12 * np.abs(u).max()
+    lev, col, sel = ad.free_vertices(S)
+    hanging = np.setdiff1d(np.nonzero(~S.boundary)[0], sel)
+    assert len(hanging) > 0
