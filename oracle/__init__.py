@@ -18,6 +18,9 @@ cycle     smoothed restriction R~ (Sec. 3.2), the adAFAC-Jac cycle (Alg. 1,
           Eq. 9) in correction-scheme and FAS/HTMG form (Eq. 4), adAFAC-PI
           (Alg. 2), plain additive multigrid (Eq. 2) with optional exponential
           damping, and the normalised residual (Eq. 10)
+adaptive  the same cycles on adaptive spacetrees with hanging vertices, over
+          the hierarchical generating system of all levels' pagodas
+          (Sec. 2.1, 2.3)
 
 Every function is pinned by ``tests/test_oracle_*.py`` against facts that do
 not come from the oracle itself (closed forms, the paper's printed stencil,
