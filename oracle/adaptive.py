@@ -407,3 +407,120 @@ def sample(sys_: AdaptiveSystem, fn) -> np.ndarray:
     """fn(x) at the leaf nodes; x has the last array axis as the x coordinate."""
     pts = sys_.coords[:, ::-1] / sys_.tree.N
     return fn(pts)
+
+
+# --------------------------------------------------------------------------
+# dynamic refinement
+# --------------------------------------------------------------------------
+
+def evaluate(sys_: AdaptiveSystem, u: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """The function of the adaptive grid's space with leaf-node values u at
+    fine-index positions pts (shape (m, d), array-axis order, integers in
+    0..N of sys_'s tree): d-linear interpolation inside the leaf cell that
+    contains each point."""
+    tree = sys_.tree
+    d, L = tree.d, tree.L
+    out = np.full(len(pts), np.nan)
+    todo = np.ones(len(pts), dtype=bool)
+    cs = np.array(corners(d))
+    for l in range(1, L + 1):
+        s = 3 ** (L - l)
+        n = 3 ** l
+        cell = np.minimum(pts // s, n - 1)             # the level-l cell holding the point
+        leaf = tree.exists[l][tuple(cell.T)] & ~tree.refined[l][tuple(cell.T)]
+        sel = todo & leaf
+        if not np.any(sel):
+            continue
+        c = cell[sel]
+        t = (pts[sel] - s * c) / s                      # local coordinates in [0, 1]
+        val = np.zeros(int(sel.sum()))
+        for b in cs:
+            w = np.prod(np.where(b == 1, t, 1.0 - t), axis=1)
+            val += w * u[sys_.node_id[tuple((s * (c + b)).T)]]
+        out[sel] = val
+        todo &= ~sel
+    return out
+
+
+def from_vertex_values(sys_: AdaptiveSystem, v: np.ndarray) -> np.ndarray:
+    """The function of the adaptive grid's space that takes the values v at
+    the vertices of the nodal space and at the boundary vertices; hanging
+    nodes get the d-linear interpolation of their coarse cell (v there is not
+    used).  Built level by level from the coarsest: the pagodas of one level
+    vanish at the other vertices of that level and at every coarser
+    position, so each level adds what the coarser ones left over."""
+    u = dirichlet_lift(sys_, v)
+    lev, col, sel = free_vertices(sys_)
+    for l in range(1, sys_.L + 1):
+        m = lev == l
+        if not np.any(m):
+            continue
+        coef = v[sel[m]] - u[sel[m]]
+        u = u + sys_.Phi[l][:, col[m]] @ coef
+    return u
+
+
+def transfer(old: AdaptiveSystem, u_old: np.ndarray, new: AdaptiveSystem) -> np.ndarray:
+    """The iterate on a changed tree: the vertices of the new tree take the
+    value of the old function at their position, i.e. new vertices are
+    d-linear interpolations of the old grid (Sec. 5: new and hanging vertices
+    are initialised by d-linear interpolation); vertices that hang in the new
+    tree take the interpolation of their new coarse cell; removed vertices
+    drop out."""
+    if old.tree.L != new.tree.L or old.tree.d != new.tree.d:
+        raise ValueError("the trees must have the same depth and dimension")
+    return from_vertex_values(new, evaluate(old, u_old, new.coords))
+
+
+def band_tree(d: int, L: int, L_base: int, centre, radius: float, width: float) -> AdaptiveTree:
+    """Depth L_base everywhere and L within `width` of the circle (sphere) of
+    the given radius about `centre` (x first): the shape of the survey's
+    adaptive workload.  A cell is refined when it reaches within width of the
+    circle, with its half-diagonal as the margin."""
+    ctr = np.asarray(centre, dtype=float)
+
+    def ref(l, c, h):
+        if l < L_base:
+            return np.ones(c.shape[:-1], dtype=bool)
+        r = np.sqrt(((c - ctr) ** 2).sum(-1))
+        return np.abs(r - radius) <= width + 0.5 * np.sqrt(d) * h
+
+    return tree_from_refinement(d, L, ref)
+
+
+def moving_band_solve(d: int, L: int, L_base: int, eps, f_fn, centre, radius: float,
+                      width: float, shift: float, every: int, moves: int, tol: float = 1e-8,
+                      max_cycles: int = 2000, **kw):
+    """Cycles on a tree whose refined band moves by `shift` along x after every
+    `every` cycles, `moves` times, then stays; the iterate is carried over by
+    transfer() at each move.  f_fn(x) gives f at points (m, d), x first.
+    Returns (system of the last tree, u, list of (cycle, relative residual
+    on the current tree))."""
+    ctr = np.array(centre, dtype=float)
+    N = 3 ** L
+    idx = np.indices((N + 1,) * d).reshape(d, -1).T
+    f = f_fn(idx[:, ::-1] / N).reshape((N + 1,) * d)
+
+    def system(c):
+        return build_system(band_tree(d, L, L_base, c, radius, width), eps, f)
+
+    S = system(ctr)
+    u = np.zeros(len(S.coords))
+    r0 = residual_norm(S, u)
+    hist = [(0, 1.0)]
+    k = 0
+    for m in range(moves + 1):
+        steps = every if m < moves else max_cycles - k
+        for _ in range(steps):
+            u = cycle(S, u, **kw)
+            k += 1
+            rel = residual_norm(S, u) / r0
+            hist.append((k, rel))
+            if m == moves and (rel <= tol or not np.isfinite(rel)):
+                return S, u, hist
+        if m < moves:
+            ctr = ctr + np.array([shift] + [0.0] * (d - 1))
+            S_new = system(ctr)
+            u = transfer(S, u, S_new)
+            S = S_new
+    return S, u, hist

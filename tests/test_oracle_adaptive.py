@@ -130,3 +130,65 @@ def test_iterates_stay_in_the_space_of_the_adaptive_grid():
     lev, col, sel = ad.free_vertices(S)
     hanging = np.setdiff1d(np.nonzero(~S.boundary)[0], sel)
     assert len(hanging) > 0
+
+
+# ---------------------------------------------------------------------------
+# dynamic refinement: the band moves, vertices are interpolated
+
+def test_vertex_values_rebuild_any_function_of_the_space():
+    d, L = 2, 4
+    S = ad.build_system(_band_tree(d, L), 1.0, wl.constant_rhs(d, L))
+    B = ad.composite_basis(S)
+    u = B @ np.random.default_rng(2).standard_normal(B.shape[1])
+    assert np.abs(ad.from_vertex_values(S, u) - u).max() <= 1e-13 * np.abs(u).max()
+
+
+def test_transfer_to_a_finer_tree_keeps_the_function():
+    d, L = 2, 4
+    coarse = ad.build_system(ad.band_tree(d, L, 2, (0.5, 0.5), 0.3, 0.03), 1.0,
+                             wl.constant_rhs(d, L))
+    fine = ad.build_system(ad.band_tree(d, L, 2, (0.5, 0.5), 0.3, 0.12), 1.0,
+                           wl.constant_rhs(d, L))
+    assert len(fine.coords) > len(coarse.coords)
+    B = ad.composite_basis(coarse)
+    u = B @ np.random.default_rng(4).standard_normal(B.shape[1])
+    v = ad.transfer(coarse, u, fine)
+    # the finer tree represents the coarse tree's function exactly
+    assert np.abs(ad.evaluate(fine, v, coarse.coords) - u).max() <= 1e-13 * np.abs(u).max()
+
+
+def test_transfer_of_a_linear_function_is_exact_both_ways():
+    d, L = 2, 4
+    a = ad.build_system(ad.band_tree(d, L, 2, (0.5, 0.5), 0.3, 0.05), 1.0, wl.constant_rhs(d, L))
+    b = ad.build_system(ad.band_tree(d, L, 2, (0.6, 0.5), 0.3, 0.05), 1.0, wl.constant_rhs(d, L))
+    lin = lambda x: 0.5 - 1.5 * x[:, 0] + 2.0 * x[:, 1]
+    ua = ad.sample(a, lin)
+    assert np.abs(ad.transfer(a, ua, b) - ad.sample(b, lin)).max() <= 1e-13
+    assert np.abs(ad.transfer(b, ad.sample(b, lin), a) - ua).max() <= 1e-13
+
+
+def test_a_band_that_does_not_move_is_the_static_solve():
+    d, L = 2, 4
+    one = lambda x: np.ones(len(x))
+    S, u, hist = ad.moving_band_solve(d, L, 2, 1.0, one, (0.5, 0.5), 0.3, 0.05, 0.0, 5, 3,
+                                      tol=1e-9)
+    Ss = ad.build_system(ad.band_tree(d, L, 2, (0.5, 0.5), 0.3, 0.05), 1.0, wl.constant_rhs(d, L))
+    us, hs = ad.solve(Ss, tol=1e-9)
+    # the same cycles; re-building the iterate at each (empty) move only
+    # rounds it (1e-16 of the values)
+    assert len(hist) == len(hs)
+    np.testing.assert_allclose([h for _, h in hist], hs, rtol=0, atol=1e-13)
+    assert np.abs(u - us).max() <= 1e-12 * np.abs(us).max()
+
+
+def test_moving_band_converges_to_the_last_trees_solution():
+    d, L = 2, 4
+    one = lambda x: np.ones(len(x))
+    S, u, hist = ad.moving_band_solve(d, L, 2, 1.0, one, (0.5, 0.5), 0.3, 0.05, 0.05, 5, 4,
+                                      tol=1e-9)
+    assert hist[-1][1] <= 1e-9
+    ud = ad.direct_solution(S)
+    assert np.abs(u - ud).max() <= 1e-7 * np.abs(ud).max()
+    # the band moved: the last tree differs from the first
+    first = ad.band_tree(d, L, 2, (0.5, 0.5), 0.3, 0.05)
+    assert not np.array_equal(first.exists[L], S.tree.exists[L])
