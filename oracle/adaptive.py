@@ -18,9 +18,11 @@ cells, hanging positions included), so
   * the level-l pagodas are the columns of Phi_l (their values at the leaf
     nodes), and the residual that level l sees is r_l = Phi_l^T (b - K u),
     the residual of the composite problem tested with level l's shape
-    functions.  This is what the FAS/HTMG right-hand sides of Eq. 4 deliver
-    with Galerkin operators; on a fully refined tree Phi_l = P^(L-l) and
-    r_l = R^(L-l) r_L (Alg. 1).
+    functions.  On a fully refined tree Phi_l = P^(L-l) and r_l = R^(L-l) r_L
+    (Alg. 1), which the FAS/HTMG form of Eq. 4 reproduces with Galerkin
+    operators; on adaptive trees this module takes the tested residual as
+    the definition (reading) and does not restate the level-wise FAS
+    traversal.
 The level operator of level l is A_l = Phi_l^T K Phi_l (Ritz-Galerkin over
 the generating system, Sec. 2.2) and M_l = diag(A_l).
 
