@@ -19,10 +19,9 @@ cells, hanging positions included), so
     nodes), and the residual that level l sees is r_l = Phi_l^T (b - K u),
     the residual of the composite problem tested with level l's shape
     functions.  On a fully refined tree Phi_l = P^(L-l) and r_l = R^(L-l) r_L
-    (Alg. 1), which the FAS/HTMG form of Eq. 4 reproduces with Galerkin
-    operators; on adaptive trees this module takes the tested residual as
-    the definition (reading) and does not restate the level-wise FAS
-    traversal.
+    (Alg. 1).  fas_level_residuals restates the level-wise FAS/HTMG form of
+    Eq. 4 on the spacetree (injection, hierarchical values, Galerkin element
+    matrices, cell by cell); the tests check that both give the same r_l.
 The level operator of level l is A_l = Phi_l^T K Phi_l (Ritz-Galerkin over
 the generating system, Sec. 2.2) and M_l = diag(A_l).
 
@@ -124,6 +123,8 @@ class AdaptiveSystem:
     active_grid: dict       # l -> (3^l+1)^d int: column of Phi_l, -1 if not active
     diag: dict              # l -> diag(Phi_l^T K Phi_l)
     S_trunc: np.ndarray     # truncated smoothed restriction stencil (5^d)
+    eps: object = None      # the inputs: eps (scalar or per fine cell), f at fine positions
+    f: np.ndarray = None
 
     @property
     def d(self) -> int:
@@ -240,7 +241,7 @@ def build_system(tree: AdaptiveTree, eps, f) -> AdaptiveSystem:
         PhiB[l], bnd[l] = pagodas(bv, s), bv
     S = rc.truncate_stencil(rc.smoothed_prolongation_stencil(d))
     return AdaptiveSystem(tree, node_id, coords, boundary, K, b, Phi, PhiB, bnd, active,
-                          active_grid, diag, S)
+                          active_grid, diag, S, eps, f)
 
 
 # --------------------------------------------------------------------------
@@ -409,6 +410,102 @@ def sample(sys_: AdaptiveSystem, fn) -> np.ndarray:
     """fn(x) at the leaf nodes; x has the last array axis as the x coordinate."""
     pts = sys_.coords[:, ::-1] / sys_.tree.N
     return fn(pts)
+
+
+# --------------------------------------------------------------------------
+# the level-wise FAS/HTMG form (Eq. 4) on the spacetree
+# --------------------------------------------------------------------------
+
+def _closure_weights(d: int) -> np.ndarray:
+    """d-linear weights W[p, e] of the 4^d closure points p of a coarse cell
+    (local coordinates 0..3, last axis fastest) towards its corners e."""
+    pts = list(itertools.product(range(4), repeat=d))
+    cs = corners(d)
+    W = np.zeros((len(pts), len(cs)))
+    for i, p in enumerate(pts):
+        for k, e in enumerate(cs):
+            W[i, k] = np.prod([pj / 3.0 if ej else 1.0 - pj / 3.0 for pj, ej in zip(p, e)])
+    return W
+
+
+def fas_level_residuals(sys_: AdaptiveSystem, u: np.ndarray) -> dict:
+    """Level residuals r_l = b_l - A_l u_l at the active vertices of every
+    level, computed cell by cell in the FAS/HTMG form of Eq. 4:
+
+      u_l = I u_{l+1}: every level holds the function's values at its
+        vertices (correction vertices the injection of the finer level,
+        hanging ones the interpolation of their coarse cell);
+      a leaf cell contributes its load and its element matrix
+        eps h^(d-2) K_ref; a refined cell contributes the Galerkin element
+        matrix K_E = sum_c W_c^T K_c W_c of its 3^d children and the
+        right-hand side b_E = sum_c W_c^T (b_c - K_c u^_c) with the
+        hierarchical values u^_c = u_c - W_c u_E of the children
+        (R r^_{l+1} with r^ = b - A u^, u^ = (id - P I) u);
+      r_l(v) = sum over the level-l cells E at v of (b_E - K_E u_E)(v).
+
+    With Galerkin element matrices this equals the residual of the composite
+    problem tested with level l's shape functions; the tests check that."""
+    tree = sys_.tree
+    d, L, N = tree.d, tree.L, tree.N
+    cs = np.array(corners(d))
+    nc = len(cs)
+    Kref = reference_element_matrix(d)
+    W = _closure_weights(d)
+    kids = np.array(list(itertools.product(range(3), repeat=d)))
+    # closure point index of every child corner: child kc, corner b -> kc + b
+    cp = np.array([[np.ravel_multi_index(tuple(kc + b), (4,) * d) for b in cs] for kc in kids])
+    Kc, bc = {}, {}           # per level: element matrices and right-hand sides of the cells
+    uvals = {}
+    for l in range(L, 0, -1):
+        n = 3 ** l
+        s = 3 ** (L - l)
+        h = 1.0 / n
+        ex = tree.exists[l]
+        K_l = np.zeros((n,) * d + (nc, nc))
+        b_l = np.zeros((n,) * d + (nc,))
+        # values of the function at every level-l vertex position
+        grid = np.indices((n + 1,) * d).reshape(d, -1).T
+        uvals[l] = np.full((n + 1,) * d, np.nan)
+        ok = np.zeros((n + 1,) * d, dtype=bool)
+        for bb in cs:
+            cells = np.argwhere(ex)
+            ok[tuple((cells + bb).T)] = True
+        pos = grid[ok.reshape(-1)]
+        uvals[l][tuple(pos.T)] = evaluate(sys_, u, s * pos)
+        leaf = ex & ~tree.refined[l]
+        cells = np.argwhere(leaf)
+        if len(cells):
+            e = _leaf_eps(sys_.eps, tree, l, cells)
+            K_l[tuple(cells.T)] = (e * h ** (d - 2))[:, None, None] * Kref
+            fv = np.stack([sys_.f[tuple((s * (cells + bb)).T)] for bb in cs], axis=1)
+            b_l[tuple(cells.T)] = (h ** d / 2 ** d) * fv
+        ref = np.argwhere(tree.refined[l]) if l < L else np.zeros((0, d), dtype=int)
+        for E in ref:
+            KE = np.zeros((nc, nc))
+            bE = np.zeros(nc)
+            uE = np.array([uvals[l][tuple(E + bb)] for bb in cs])
+            for ci, kc in enumerate(kids):
+                child = tuple(3 * E + kc)
+                Wc = W[cp[ci]]                          # child's corners x coarse corners
+                Kk = Kc[l + 1][child]
+                uc = np.array([uvals[l + 1][tuple(3 * E + kc + bb)] for bb in cs])
+                uhat = uc - Wc @ uE
+                KE += Wc.T @ Kk @ Wc
+                bE += Wc.T @ (bc[l + 1][child] - Kk @ uhat)
+            K_l[tuple(E)] = KE
+            b_l[tuple(E)] = bE
+        Kc[l], bc[l] = K_l, b_l
+    out = {}
+    for l in range(1, L + 1):
+        n = 3 ** l
+        r = np.zeros((n + 1,) * d)
+        cells = np.argwhere(tree.exists[l])
+        uE = np.stack([uvals[l][tuple((cells + bb).T)] for bb in cs], axis=1)
+        contrib = bc[l][tuple(cells.T)] - np.einsum("mab,mb->ma", Kc[l][tuple(cells.T)], uE)
+        for k, bb in enumerate(cs):
+            np.add.at(r, tuple((cells + bb).T), contrib[:, k])
+        out[l] = r[tuple(sys_.active[l].T)]
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -192,3 +192,22 @@ def test_moving_band_converges_to_the_last_trees_solution():
     # the band moved: the last tree differs from the first
     first = ad.band_tree(d, L, 2, (0.5, 0.5), 0.3, 0.05)
     assert not np.array_equal(first.exists[L], S.tree.exists[L])
+
+
+@pytest.mark.parametrize("d,L,tree", [(2, 3, "corner"), (2, 4, "band"), (3, 3, "corner"),
+                                      (2, 3, "regular")])
+def test_level_wise_fas_htmg_gives_the_tested_residuals(d, L, tree):
+    # Eq. 4 on the spacetree, cell by cell (injection, hierarchical values,
+    # Galerkin element matrices of refined cells) against the composite
+    # residual tested with every level's pagodas
+    T = {"corner": _corner_tree, "band": _band_tree,
+         "regular": lambda d, L: ad.regular_tree(d, L)}[tree](d, L)
+    N = 3 ** L
+    eps = np.random.default_rng(3).uniform(0.2, 3.0, size=(N,) * d)
+    S = ad.build_system(T, eps, wl.manufactured_rhs(d, L))
+    B = ad.composite_basis(S)
+    u = B @ np.random.default_rng(1).standard_normal(B.shape[1])
+    rf = ad.fas_level_residuals(S, u)
+    rg = ad.level_residuals(S, u)
+    for l in rg:
+        assert np.abs(rf[l] - rg[l]).max() <= 1e-13 * np.abs(rg[l]).max(), l
