@@ -198,19 +198,24 @@ def build_system(tree: AdaptiveTree, eps, f) -> AdaptiveSystem:
     Phi, active, active_grid, diag, PhiB, bnd = {}, {}, {}, {}, {}, {}
 
     def pagodas(verts, s):
-        # values of the pagodas of width s (fine units) at the leaf nodes,
-        # truncated to the domain
+        # values of the pagodas of width s (fine units) centred at the level
+        # vertices verts, at the leaf nodes (truncated to the domain): a leaf
+        # node p lies in the level cell floor(p / s), and only that cell's 2^d
+        # corners v have pagodas that reach it, with the value
+        # prod_k (1 - |p_k - s v_k| / s)
+        n = N // s
+        col = -np.ones((n + 1,) * d, dtype=np.int64)
+        col[tuple(verts.T)] = np.arange(len(verts))
+        cell = np.minimum(coords // s, n - 1)
         r_, c_, v_ = [], [], []
-        for off in itertools.product(range(-s + 1, s), repeat=d):
-            w = np.prod([1.0 - abs(o) / s for o in off])
-            pos = s * verts + np.array(off)
-            inside = np.all((pos >= 0) & (pos <= N), axis=1)
-            ids = -np.ones(len(verts), dtype=np.int64)
-            ids[inside] = node_id[tuple(pos[inside].T)]
-            ok = ids >= 0
-            r_.append(ids[ok])
-            c_.append(np.nonzero(ok)[0])
-            v_.append(np.full(int(ok.sum()), w))
+        for bb in cs:
+            v = cell + bb
+            w = np.prod(1.0 - np.abs(coords - s * v) / s, axis=1)
+            j = col[tuple(v.T)]
+            ok = (j >= 0) & (w > 0.0)
+            r_.append(np.nonzero(ok)[0])
+            c_.append(j[ok])
+            v_.append(w[ok])
         return sp.csr_matrix((np.concatenate(v_), (np.concatenate(r_), np.concatenate(c_))),
                              shape=(len(coords), len(verts)))
 
