@@ -628,3 +628,165 @@ def moving_band_solve(d: int, L: int, L_base: int, eps, f_fn, centre, radius: fl
             u = transfer(S, u, S_new)
             S = S_new
     return S, u, hist
+
+
+# --------------------------------------------------------------------------
+# the adaptive runs of Sec. 5: refinement at the boundary and by derivatives
+# --------------------------------------------------------------------------
+
+def refine_cells(tree: AdaptiveTree, l: int, cells: np.ndarray) -> AdaptiveTree:
+    """A copy of the tree with the given existing leaf cells of level l < L
+    cut into their 3^d children."""
+    d, L = tree.d, tree.L
+    exists = {k: v.copy() for k, v in tree.exists.items()}
+    refined = {k: v.copy() for k, v in tree.refined.items()}
+    for k in range(1, L + 1):
+        exists.setdefault(k, np.zeros((3 ** k,) * d, dtype=bool))
+    if len(cells):
+        refined[l][tuple(cells.T)] = True
+        for c in cells:
+            exists[l + 1][tuple(slice(3 * ck, 3 * ck + 3) for ck in c)] = True
+    return AdaptiveTree(d, L, exists, refined)
+
+
+def coarse_tree(d: int, L: int, depth: int) -> AdaptiveTree:
+    """Regular up to level `depth`, no cells below: the start of the runs
+    (Sec. 5 starts from a two-grid scheme, depth 2)."""
+    T = tree_from_refinement(d, L, lambda l, c, h: np.full(c.shape[:-1], l < depth))
+    return T
+
+
+def second_derivative_indicator(sys_: AdaptiveSystem, u: np.ndarray):
+    """Largest absolute second difference along the coordinate axes at every
+    vertex of the nodal space, on the spacing of its level (Sec. 5: absolute
+    second derivatives along both axes in every unknown).  Returns (levels,
+    level indices (m, d), values)."""
+    lev, col, sel = free_vertices(sys_)
+    L, N = sys_.L, sys_.tree.N
+    vals = np.zeros(len(sel))
+    vidx = np.zeros((len(sel), sys_.d), dtype=np.int64)
+    for l in range(1, L + 1):
+        m = lev == l
+        if not np.any(m):
+            continue
+        v = sys_.active[l][col[m]]
+        vidx[m] = v
+        s = 3 ** (L - l)
+        h = 1.0 / 3 ** l
+        centre = u[sel[m]]
+        best = np.zeros(int(m.sum()))
+        for k in range(sys_.d):
+            e = np.zeros(sys_.d, dtype=np.int64)
+            e[k] = s
+            up = evaluate(sys_, u, np.minimum(s * v + e, N))
+            dn = evaluate(sys_, u, np.maximum(s * v - e, 0))
+            best = np.maximum(best, np.abs(up - 2.0 * centre + dn) / h ** 2)
+        vals[m] = best
+    return lev, vidx, vals
+
+
+def _top_fraction(vals: np.ndarray, fraction: float, bins: int = 64) -> np.ndarray:
+    """Indices of (approximately) the largest `fraction` of vals, by a bin
+    sort over [0, max]: the highest bins are taken while they fit the share
+    (at least the top bin)."""
+    if len(vals) == 0 or vals.max() <= 0.0:
+        return np.zeros(0, dtype=np.int64)
+    edges = np.linspace(0.0, vals.max(), bins + 1)
+    which = np.minimum(np.searchsorted(edges, vals, side="right") - 1, bins - 1)
+    target = fraction * len(vals)
+    taken = np.zeros(len(vals), dtype=bool)
+    count = 0
+    for b in range(bins - 1, -1, -1):
+        in_bin = which == b
+        n_b = int(in_bin.sum())
+        if count > 0 and count + n_b > target:
+            break
+        taken |= in_bin
+        count += n_b
+    return np.nonzero(taken)[0]
+
+
+def amr_step(sys_: AdaptiveSystem, u: np.ndarray, lmax: int, fraction: float = 0.1,
+             bottom: bool = True) -> AdaptiveTree:
+    """One refinement of Sec. 5's runs: the leaf cells along the bottom
+    boundary x_2 = 0 (where u = 1 is prescribed), and the leaf cells around
+    the vertices with the (about) `fraction` largest second derivatives,
+    unless they are on level lmax already."""
+    tree = sys_.tree
+    d = tree.d
+    ax2 = d - 2                                   # array axis of x_2
+    new = tree
+    to_refine = {l: set() for l in range(1, lmax)}
+    for l in range(1, lmax):
+        leaf = tree.exists[l] & ~tree.refined[l]
+        if bottom:
+            sl = [slice(None)] * d
+            sl[ax2] = 0
+            cells = np.argwhere(leaf[tuple(sl)])
+            for c in cells:
+                full = list(c)
+                full.insert(ax2, 0)
+                to_refine[l].add(tuple(full))
+    lev, vidx, vals = second_derivative_indicator(sys_, u)
+    for i in _top_fraction(vals, fraction):
+        l = int(lev[i])
+        if l >= lmax:
+            continue
+        leaf = tree.exists[l] & ~tree.refined[l]
+        for bb in corners(d):
+            c = vidx[i] - 1 + np.array(bb)
+            if np.all(c >= 0) and np.all(c < 3 ** l) and leaf[tuple(c)]:
+                to_refine[l].add(tuple(int(x) for x in c))
+    for l in range(1, lmax):
+        if to_refine[l]:
+            new = refine_cells(new, l, np.array(sorted(to_refine[l])))
+    return new
+
+
+def amr_solve(d: int, lmax: int, g_fn, f_fn=None, eps=1.0, start_depth: int = 2,
+              every: int = 2, tol: float = 1e-8, max_cycles: int = 400, **kw):
+    """Sec. 5's adaptive runs: start from a regular depth-`start_depth` tree,
+    refine (amr_step) after every `every` cycles, carry the iterate over by
+    d-linear interpolation, cycle until the normalised residual on the
+    current tree reaches tol once the tree has stopped changing.
+
+    Returns (system, u, history of (cycle, normalised residual, dof updates
+    so far)): the cost counts every level's active vertices per cycle (the
+    paper's "dof updates plus updates on coarser levels")."""
+    N = 3 ** lmax
+    idx = np.indices((N + 1,) * d).reshape(d, -1).T
+    pts = idx[:, ::-1] / N
+    f = (f_fn(pts) if f_fn else np.zeros(len(pts))).reshape((N + 1,) * d)
+
+    def system(tree):
+        return build_system(tree, eps, f)
+
+    S = system(coarse_tree(d, lmax, start_depth))
+    u = from_vertex_values(S, sample(S, g_fn))
+    r0 = residual_norm(S, u)
+    updates = 0
+    hist = [(0, 1.0, 0)]
+    changed = True
+    for k in range(1, max_cycles + 1):
+        u = cycle(S, u, **kw)
+        updates += sum(len(S.active[l]) for l in range(1, lmax + 1))
+        rel = residual_norm(S, u) / r0
+        hist.append((k, rel, updates))
+        if not np.isfinite(rel) or rel > 1e6:
+            break
+        if not changed and rel <= tol:
+            break
+        if k % every == 0:
+            T = amr_step(S, u, lmax)
+            changed = any(not np.array_equal(T.exists[l], S.tree.exists[l])
+                          for l in range(1, lmax + 1))
+            if changed:
+                S_new = system(T)
+                u = transfer(S, u, S_new)
+                # the boundary values of new boundary vertices come from g
+                g = sample(S_new, g_fn)
+                v = evaluate(S_new, u, S_new.coords)
+                v[S_new.boundary] = g[S_new.boundary]
+                u = from_vertex_values(S_new, v)
+                S = S_new
+    return S, u, hist

@@ -211,3 +211,43 @@ def test_level_wise_fas_htmg_gives_the_tested_residuals(d, L, tree):
     rg = ad.level_residuals(S, u)
     for l in rg:
         assert np.abs(rf[l] - rg[l]).max() <= 1e-13 * np.abs(rg[l]).max(), l
+
+
+# ---------------------------------------------------------------------------
+# the adaptive runs of Sec. 5
+
+def test_second_derivative_indicator_is_exact_for_quadratics():
+    d, L = 2, 3
+    S = ad.build_system(_corner_tree(d, L), 1.0, wl.constant_rhs(d, L))
+    lin = ad.from_vertex_values(S, ad.sample(S, lambda x: 2.0 * x[:, 0] - x[:, 1]))
+    assert np.abs(ad.second_derivative_indicator(S, lin)[2]).max() <= 1e-9
+    # u = x^2 - 3 y^2 (nodal values): central second differences give 2 and 6
+    quad = ad.from_vertex_values(S, ad.sample(S, lambda x: x[:, 0] ** 2 - 3.0 * x[:, 1] ** 2))
+    lev, vidx, vals = ad.second_derivative_indicator(S, quad)
+    # vertices whose axis neighbours are vertices of the nodal space on their
+    # own level (away from hanging nodes) see the exact values
+    interior = np.all((vidx >= 1) & (vidx <= 3 ** lev[:, None] - 1), axis=1)
+    assert np.isclose(np.median(vals[interior]), 6.0, rtol=1e-9)
+
+
+def test_top_fraction_takes_the_largest_values():
+    v = np.random.default_rng(0).exponential(size=5000)
+    sel = ad._top_fraction(v, 0.1)
+    assert 0.05 * len(v) <= len(sel) <= 0.1 * len(v)
+    rest = np.setdiff1d(np.arange(len(v)), sel)
+    assert v[sel].min() >= v[rest].max() - v.max() / 64    # within one bin
+
+
+def test_amr_run_refines_the_bottom_and_converges_to_the_composite_solution():
+    d, lmax = 2, 4
+    bottom = lambda x: (x[:, 1] == 0).astype(float)
+    S, u, hist = ad.amr_solve(d, lmax, bottom, tol=1e-8, max_cycles=300)
+    assert hist[-1][1] <= 1e-8
+    # every cell along x_2 = 0 reaches the finest level
+    assert np.all(S.tree.exists[lmax][0, :])
+    # the tree is adaptive, not regular
+    assert not np.all(S.tree.exists[lmax])
+    ud = ad.direct_solution(S, ad.sample(S, bottom))
+    assert np.abs(u - ud).max() <= 1e-7
+    # the cost counts every level's active vertices per cycle
+    assert hist[-1][2] == pytest.approx(sum(h[2] - p[2] for h, p in zip(hist[1:], hist[:-1])))
