@@ -251,3 +251,15 @@ def test_amr_run_refines_the_bottom_and_converges_to_the_composite_solution():
     assert np.abs(u - ud).max() <= 1e-7
     # the cost counts every level's active vertices per cycle
     assert hist[-1][2] == pytest.approx(sum(h[2] - p[2] for h, p in zip(hist[1:], hist[:-1])))
+
+
+def test_adafac_jac_converges_on_an_adaptive_run_across_a_strong_material_jump():
+    # Sec. 5.2: with d-linear transfers adAFAC-Jac converges for every jump
+    # eps = 10^-k tested; here the halves setup, eps = 1e-7 right of x_1 = 1/2
+    d, lmax = 2, 5
+    bottom = lambda x: (x[:, 1] == 0).astype(float)
+    eps = wl.eps_halves(d, lmax, 1e-7)
+    S, u, hist = ad.amr_solve(d, lmax, bottom, eps=eps, tol=1e-8, max_cycles=400, variant="jac")
+    assert hist[-1][1] <= 1e-8
+    ud = ad.direct_solution(S, ad.sample(S, bottom))
+    assert np.abs(u - ud).max() <= 1e-6
