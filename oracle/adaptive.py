@@ -380,22 +380,25 @@ def dirichlet_lift(sys_: AdaptiveSystem, g: np.ndarray) -> np.ndarray:
     position on the finest level where it is a boundary vertex surrounded by
     its level's cells.  Boundary nodes that hang take the interpolated value
     (g there is not used)."""
-    finest = {}
+    # finest level on which each boundary node is a surrounded boundary vertex
+    finest = -np.ones(len(sys_.coords), dtype=np.int64)
+    col = -np.ones(len(sys_.coords), dtype=np.int64)
     for l in range(1, sys_.L + 1):
         s = 3 ** (sys_.L - l)
-        for k, v in enumerate(sys_.bnd[l]):
-            finest[tuple(s * v)] = (l, k)
+        ids = sys_.node_id[tuple((s * sys_.bnd[l]).T)]
+        finest[ids] = l
+        col[ids] = np.arange(len(ids))
     # the pagodas are hierarchical, not nodal: a coarse one is non-zero at
-    # finer positions, a fine one vanishes at every coarser position.  So the
-    # positions are set from the coarsest level down, each with the part of
-    # g the coarser pagodas have not produced there yet.
+    # finer positions, a fine one vanishes at every coarser position and at
+    # the other vertices of its level.  So the levels are set from the
+    # coarsest down, each with the part of g the coarser pagodas have not
+    # produced there yet.
     u = np.zeros(len(sys_.coords))
-    for lev in range(1, sys_.L + 1):
-        for pos, (l, k) in finest.items():
-            if l != lev:
-                continue
-            i = sys_.node_id[pos]
-            u += (g[i] - u[i]) * sys_.PhiB[l][:, k].toarray().ravel()
+    for l in range(1, sys_.L + 1):
+        ids = np.nonzero(finest == l)[0]
+        if len(ids) == 0:
+            continue
+        u = u + sys_.PhiB[l][:, col[ids]] @ (g[ids] - u[ids])
     return u
 
 
