@@ -279,7 +279,7 @@ adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
  * problem shape (dim, depth, path, eps kind, transfer, variant, lmin): a later
  * handle of the same shape takes them without timing (cached = 1).
  * The call synchronises the handle's stream, runs only on the handle's
- * arrays (it allocates nothing), and resets the cycle state (control block,
+ * arrays (no device memory is allocated), and resets the cycle state (control block,
  * history, correction buffers; not the iterate u): call it after setup and
  * before cycling.  *out is a caller-owned record, filled on success.
  * Returns INVALID_ARG (null argument, repeats out of range) or CUDA. */
