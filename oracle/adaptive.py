@@ -436,7 +436,7 @@ def _closure_weights(d: int) -> np.ndarray:
     return W
 
 
-def fas_level_residuals(sys_: AdaptiveSystem, u: np.ndarray) -> dict:
+def fas_level_residuals(sys_: AdaptiveSystem, u: np.ndarray, return_diag: bool = False):
     """Level residuals r_l = b_l - A_l u_l at the active vertices of every
     level, computed cell by cell in the FAS/HTMG form of Eq. 4:
 
@@ -452,7 +452,9 @@ def fas_level_residuals(sys_: AdaptiveSystem, u: np.ndarray) -> dict:
       r_l(v) = sum over the level-l cells E at v of (b_E - K_E u_E)(v).
 
     With Galerkin element matrices this equals the residual of the composite
-    problem tested with level l's shape functions; the tests check that."""
+    problem tested with level l's shape functions; the tests check that.
+    return_diag also returns every level's diagonal sum_E K_E(v, v) at the
+    active vertices (M_l of the Jacobi steps)."""
     tree = sys_.tree
     d, L, N = tree.d, tree.L, tree.N
     cs = np.array(corners(d))
@@ -503,17 +505,21 @@ def fas_level_residuals(sys_: AdaptiveSystem, u: np.ndarray) -> dict:
             K_l[tuple(E)] = KE
             b_l[tuple(E)] = bE
         Kc[l], bc[l] = K_l, b_l
-    out = {}
+    out, diag = {}, {}
     for l in range(1, L + 1):
         n = 3 ** l
         r = np.zeros((n + 1,) * d)
+        dg = np.zeros((n + 1,) * d)
         cells = np.argwhere(tree.exists[l])
         uE = np.stack([uvals[l][tuple((cells + bb).T)] for bb in cs], axis=1)
-        contrib = bc[l][tuple(cells.T)] - np.einsum("mab,mb->ma", Kc[l][tuple(cells.T)], uE)
+        KE = Kc[l][tuple(cells.T)]
+        contrib = bc[l][tuple(cells.T)] - np.einsum("mab,mb->ma", KE, uE)
         for k, bb in enumerate(cs):
             np.add.at(r, tuple((cells + bb).T), contrib[:, k])
+            np.add.at(dg, tuple((cells + bb).T), KE[:, k, k])
         out[l] = r[tuple(sys_.active[l].T)]
-    return out
+        diag[l] = dg[tuple(sys_.active[l].T)]
+    return (out, diag) if return_diag else out
 
 
 # --------------------------------------------------------------------------

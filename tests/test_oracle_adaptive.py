@@ -207,10 +207,12 @@ def test_level_wise_fas_htmg_gives_the_tested_residuals(d, L, tree):
     S = ad.build_system(T, eps, wl.manufactured_rhs(d, L))
     B = ad.composite_basis(S)
     u = B @ np.random.default_rng(1).standard_normal(B.shape[1])
-    rf = ad.fas_level_residuals(S, u)
+    rf, dg = ad.fas_level_residuals(S, u, return_diag=True)
     rg = ad.level_residuals(S, u)
     for l in rg:
         assert np.abs(rf[l] - rg[l]).max() <= 1e-13 * np.abs(rg[l]).max(), l
+        # the Jacobi diagonal from the cells' Galerkin element matrices
+        assert np.abs(dg[l] - S.diag[l]).max() <= 1e-13 * S.diag[l].max(), l
 
 
 # ---------------------------------------------------------------------------
