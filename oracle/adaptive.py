@@ -587,8 +587,9 @@ def transfer(old: AdaptiveSystem, u_old: np.ndarray, new: AdaptiveSystem) -> np.
 
 def band_tree(d: int, L: int, L_base: int, centre, radius: float, width: float) -> AdaptiveTree:
     """Depth L_base everywhere and L within `width` of the circle (sphere) of
-    the given radius about `centre` (x first): the shape of the survey's
-    adaptive workload.  A cell is refined when it reaches within width of the
+    the given radius about `centre` (x first): the shape of the adaptive
+    workload (depth 8 within 0.05 of the circle r = 0.3 about the centre,
+    depth 3 elsewhere).  A cell is refined when it reaches within width of the
     circle, with its half-diagonal as the margin."""
     ctr = np.asarray(centre, dtype=float)
 
