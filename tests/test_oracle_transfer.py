@@ -95,6 +95,38 @@ def test_boxmg_gamma_points_for_eps_varying_along_x():
                 assert got_right == pytest.approx(1.0 - want_left, rel=1e-12)
 
 
+def test_boxmg_3d_points_for_eps_varying_along_x():
+    # 3-D, eps depends on x only.  gamma points on coarse edges along x: the
+    # stencil collapsed along y and z is again the 1-D flux operator, so the
+    # weights are linear in the resistance.  gamma points on coarse faces
+    # normal to x: collapsed along x the operator in (y, z) has constant
+    # coefficients, so the weights are the bilinear ones.
+    rng = np.random.default_rng(12)
+    d, n_f, n_c = 3, 9, 3
+    col = rng.uniform(1e-3, 1.0, size=n_f)
+    eps = np.broadcast_to(col[None, None, :], (n_f,) * 3).copy()
+    W = transfer.boxmg_closure_weights(
+        fem.LevelOperator.from_eps(d, n_f, eps, False).stencils(), n_c)
+    pidx = {l: k for k, l in enumerate(transfer.closure_points(3))}
+    cidx = {c: k for k, c in enumerate(fem.corners(3))}
+    Ex = 1                                  # both edge ends interior
+    res = 1.0 / col[3 * Ex:3 * Ex + 3]
+    for Ez in (1, 2):
+        for Ey in (1, 2):
+            for lx in (1, 2):
+                want = res[lx:].sum() / res.sum()
+                w0 = W[Ez, Ey, Ex, pidx[(0, 0, lx)], cidx[(0, 0, 0)]]
+                w1 = W[Ez, Ey, Ex, pidx[(0, 0, lx)], cidx[(0, 0, 1)]]
+                assert w0 == pytest.approx(want, rel=1e-12)
+                assert w1 == pytest.approx(1.0 - want, rel=1e-12)
+    # the face x = 3 Ex of the interior cell (1, 1, 1), all of whose corners
+    # are interior vertices
+    for ly in (1, 2):
+        for lz in (1, 2):
+            w = W[1, 1, 1, pidx[(lz, ly, 0)], cidx[(0, 0, 0)]]
+            assert w == pytest.approx((1 - ly / 3) * (1 - lz / 3), rel=1e-12)
+
+
 @pytest.mark.parametrize("d,L", [(2, 3), (3, 2)])
 def test_boxmg_fpoint_equations_hold(d, L):
     # the defining property: (A P e)_f = 0 at every f-point, checked with the
