@@ -193,6 +193,21 @@ adafac_status adafac_set_boundary(adafac_handle h, const double* g, int g_on_dev
  * Asynchronous (a device kernel resets the control block). */
 adafac_status adafac_reset(adafac_handle h);
 
+/* Poll limit of the bounded device-side waits on h.  The fused 3-D sweeps
+ * stage their planes by asynchronous copies and wait for each on a shared
+ * memory barrier; a wait gives up after `polls` polls or 2 s of device time,
+ * whichever comes first (default 4194304 polls).  A wait that gives up stores
+ * nothing of its step, its block leaves, the kernels after it in the batch
+ * return at entry, and the next synchronising call returns
+ * ADAFAC_ERR_TIMEOUT naming where the first wait gave up (adafac_last_error).
+ * polls = 0 makes every wait give up before its first poll, so the timeout
+ * path can be exercised without a copy that never lands; the iterate then
+ * keeps its value from before the batch.  adafac_reset clears the fault.
+ * The paper has no counterpart (its code runs on CPUs).  Handles off the
+ * fused path have no such waits and ignore the value.  INVALID_ARG for
+ * polls < 0.  Synchronises (cycles already enqueued keep the old limit). */
+adafac_status adafac_set_wait_limit(adafac_handle h, long long polls);
+
 /* Inspection of internal per-level arrays (for tests and diagnostics).
  * field: ADAFAC_FIELD_*; level: 1..L.  Copies the array as doubles to dst
  * (host or device) and writes its length to *count (pass dst = NULL to query
@@ -297,14 +312,20 @@ typedef struct {
 } adafac_tuning;
 adafac_status adafac_autotune(adafac_handle h, int repeats, adafac_tuning* out);
 
-/* ||b - A u||_h (Eq. 10) for the uniform d-linear operator of
- * -div(eps grad u) with scalar eps (Sec. 2.1) on a regular tree of depth
- * `depth` in `dim` = 2 or 3 dimensions, computed WITHOUT ALLOCATING device
- * memory.  The paper has no counterpart: this entry exists for callers that
- * cannot allocate (a process whose device memory is fully committed, or one
- * that must not pay the synchronisation of a device free).
- *   u, b  device arrays of (3^depth + 1)^dim doubles, x fastest, boundary
- *         ring included (its values are ignored); caller-owned, read only.
+/* sqrt(h^dim * sum over the interior vertices i of r_i^2), r = b - A u, where
+ * A is the uniform d-linear finite-element stencil of -div(eps grad u) with
+ * scalar eps and h = 3^-depth, on a regular grid of 3^depth cells per axis in
+ * `dim` = 2 or 3 dimensions, computed WITHOUT ALLOCATING device memory.
+ * The paper has no counterpart.  This entry exists for callers that cannot
+ * allocate: a process whose device memory is fully committed to resident
+ * workspaces, or code that must not pay the device-wide synchronisation of a
+ * device free.
+ *   u     device array of (3^depth + 1)^dim doubles, x fastest, boundary ring
+ *         included.  The stencil of a vertex next to the boundary reads the
+ *         ring, so the ring must hold the Dirichlet values (zero for
+ *         homogeneous problems); caller-owned, read only.
+ *   b     device array of the same shape; only its interior values are read
+ *         (its ring is ignored); caller-owned, read only.
  *   norm  device pointer to one double, written asynchronously on `stream`
  *         (a cudaStream_t, NULL = legacy default stream).
  * The per-block partial sums live in a fixed device array of the library
@@ -312,13 +333,15 @@ adafac_status adafac_autotune(adafac_handle h, int repeats, adafac_tuning* out);
  * 4096 * 16384 = 67,108,864 vertices; larger trees return INVALID_ARG without
  * launching.  Nothing in that array needs to start at zero: every partial the
  * norm reads is written by the same call.
- * The first call on each device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * outside any stream capture.  The array is shared by all calls on a device:
- * calls that overlap in time (other streams, other host threads) race on it
- * and may return wrong norms; order them on one stream.
+ * The array exists once per CUDA context.  The first call in each context
+ * (also after a cudaDeviceReset, which makes a new context) looks up its
+ * address with cudaGetSymbolAddress; make that first call outside any stream
+ * capture (under capture it returns CUDA).  All calls in a context share the
+ * array: calls that overlap in time (other streams, other host threads) race
+ * on it and may return wrong norms; order them on one stream.
  * Returns INVALID_ARG (bad dim/depth/eps, null pointer, tree too large) or
- * CUDA (launch failure); adafac_last_error is not updated by this call. */
+ * CUDA (launch failure, or the first call of a context made under capture);
+ * adafac_last_error is not updated by this call. */
 adafac_status adafac_residual_norm_static(int dim, int depth, double eps, const double* u,
                                          const double* b, double* norm, void* stream);
 

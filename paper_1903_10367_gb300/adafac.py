@@ -88,6 +88,7 @@ _SIGNATURES = [
     ("adafac_set_solution", _I, [_P, _P, _I]),
     ("adafac_set_boundary", _I, [_P, _P, _I]),
     ("adafac_reset", _I, [_P]),
+    ("adafac_set_wait_limit", _I, [_P, ctypes.c_longlong]),
     ("adafac_get_field", _I, [_P, _I, _I, _P, _I, ctypes.POINTER(ctypes.c_size_t)]),
     ("adafac_history", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
     ("adafac_launch_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -153,10 +154,13 @@ def workspace_size(dim: int, depth: int, opts: Options) -> int:
 
 
 def residual_norm_static(dim: int, depth: int, eps: float, u, b, norm, stream=None):
-    """||b - A u||_h (Eq. 10) of the uniform operator on device tensors u, b
-    ((3^depth+1)^dim float64 each), written into the 1-element float64 device
-    tensor ``norm`` on ``stream`` (default: torch's current stream).  The library
-    allocates nothing for this call (adafac_residual_norm_static)."""
+    """sqrt(h^dim * sum over interior vertices of r^2), r = b - A u with the
+    uniform d-linear stencil of -div(eps grad u), on device tensors u, b
+    ((3^depth+1)^dim float64 each; u's boundary ring holds the Dirichlet
+    values, b's is ignored), written into the 1-element float64 device tensor
+    ``norm`` on ``stream`` (default: torch's current stream).  The library
+    allocates nothing for this call (adafac_residual_norm_static), for callers
+    that cannot allocate device memory."""
     import torch
     lib = load()
     for t in (u, b, norm):
@@ -259,6 +263,11 @@ class Solver:
         else:
             _check(self.lib.adafac_solution(self.h, ctypes.c_void_p(out.data_ptr()), 1), self.h)
         return out
+
+    def set_wait_limit(self, polls: int):
+        """Poll limit of the sweeps' bounded waits (0: every wait gives up at
+        once, which exercises the timeout path)."""
+        _check(self.lib.adafac_set_wait_limit(self.h, int(polls)), self.h)
 
     def set_solution(self, u):
         if isinstance(u, np.ndarray):

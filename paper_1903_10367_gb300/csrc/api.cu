@@ -1212,6 +1212,13 @@ adafac_status adafac_setup(const adafac_tree* tree, const double* eps, int eps_i
                                : run_setup<3>(h, eps, f, inputs_on_device);
   if (st != ADAFAC_OK) {
     g_setup_error = h->err;
+    // the memset and setup kernels may still run on the stream: a caller-owned
+    // workspace (a server's pool range) must not be handed on before they end
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->own_ws) cudaFree(h->ws);
     delete h;
     return st;
@@ -1427,6 +1434,17 @@ adafac_status adafac_history(adafac_handle h, double* dst, int max_entries, int*
     if (cudaMemcpy(dst, h->hist, sizeof(double) * m, cudaMemcpyDeviceToHost) != cudaSuccess)
       return check_cuda(h, "copy history");
   }
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_set_wait_limit(adafac_handle h, long long polls) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (polls < 0) return fail(h, ADAFAC_ERR_INVALID_ARG, "polls must be >= 0");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "synchronise");
+  h->sw.wait_polls = polls;
+  // captured batches hold the sweeps' parameters by value: capture again
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
   return ADAFAC_OK;
 }
 

@@ -148,8 +148,10 @@ __device__ __forceinline__ T p_corner_weight(const LevelView<T>& lf, const int* 
   return lf.P[(long long)e * lf.V + fv];
 }
 
+// a kernel of a batch returns at entry once the solve has converged or
+// diverged, or once a bounded device-side wait of an earlier kernel gave up
 __device__ __forceinline__ bool halted(const Control* ctl) {
-  return ctl && (ctl->done || ctl->diverged);
+  return ctl && (ctl->done || ctl->diverged || ctl->fault);
 }
 
 }  // namespace adafac

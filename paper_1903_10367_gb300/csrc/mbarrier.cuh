@@ -48,11 +48,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // bounded wait on a phase of an mbarrier: gives up after kWaitNs of device
-// time or kWaitLimit polls, whichever comes first
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// time or `limit` polls (kWaitLimit by default), whichever comes first;
+// limit 0 gives up before the first poll
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kWaitLimit) {
+  if (limit <= 0) return false;
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
-  for (long i = 0; i < kWaitLimit; ++i) {
+  for (long long i = 1; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
   }

@@ -1,5 +1,6 @@
-// adafac_residual_norm_static: the Eq. 10 norm of b - A u for a uniform
-// d-linear operator, computed without allocating device memory.
+// adafac_residual_norm_static: the residual norm sqrt(h^D sum_i r_i^2) of
+// r = b - A u for a uniform d-linear operator, computed without allocating
+// device memory.
 //
 // Callers that cannot allocate: a solver service whose device memory is fully
 // committed to resident workspaces (any allocation may fail or evict), and
@@ -8,10 +9,16 @@
 // keep their per-block partial sums in a file-scope device array instead of a
 // workspace.
 //
-// The scratch array is one per device (one per CUDA context that loads this
-// library).  Calls that overlap in time on one device -- on different streams
-// or from different host threads without ordering -- race on it and may
-// return wrong norms; order them on one stream.
+// The scratch array exists once per CUDA context that loads this library.
+// Calls that overlap in time in one context -- on different streams or from
+// different host threads without ordering -- race on it and may return wrong
+// norms; order them on one stream.  Its device address is looked up once per
+// context (keyed by the context's id, which a context re-created after
+// cudaDeviceReset does not share), so the first call in each context must
+// come before any stream capture; under capture a context without a cached
+// address is refused.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "adafac.h"
@@ -25,16 +32,22 @@ namespace {
 constexpr int kMaxPartials = 4096;
 constexpr int kThreads = 256;
 constexpr long long kVertsPerBlock = 64LL * kThreads;  // 16384
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 static __device__ __align__(256) double g_partials[kMaxPartials];
 
+// cached device addresses of the scratch array, by context id
+struct Cached {
+  unsigned long long ctx = 0;
+  double* addr = nullptr;
+};
 std::mutex g_lock;
-double* g_addr[kMaxDevices] = {};
+Cached g_cache[kMaxContexts];
+int g_next = 0;
 
 // Partial sums of h^D r^2 over the interior vertices of one block's range,
 // r = b - A u with A the assembled uniform stencil of -div(eps grad) on the
-// d-linear element (Sec. 2.1): the neighbour at offset o with k non-zero
+// d-linear finite element: the neighbour at offset o with k non-zero
 // components shares 2^(D-k) cells with the centre, each contributing
 // eps h^(D-2) K_ref(k).  Every partial is written, none accumulated.
 template <int D>
@@ -94,16 +107,60 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) out[0] = sqrt(red[0]);
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current).
-double* scratch_address(int dev) {
+// Id of the current CUDA context (unique for the life of the process), or 0
+// when it cannot be read.  The driver entry points are taken through the
+// runtime, so the library needs no link against the driver library.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(fn);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context: looked up
+// (cudaGetSymbolAddress, with the context current) the first time a context is
+// seen, and refused (nullptr) when that first time falls inside a stream
+// capture on `s`.
+double* scratch_address(cudaStream_t s) {
+  const unsigned long long ctx = current_context_id();
+  if (!ctx) return nullptr;
   std::lock_guard<std::mutex> g(g_lock);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess) return nullptr;
-    g_addr[dev] = static_cast<double*>(p);
+  for (const Cached& c : g_cache)
+    if (c.ctx == ctx) return c.addr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;
   }
-  return g_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  Cached& slot = g_cache[g_next];
+  g_next = (g_next + 1) % kMaxContexts;
+  slot.ctx = ctx;
+  slot.addr = static_cast<double*>(p);
+  return slot.addr;
 }
 
 }  // namespace
@@ -126,12 +183,9 @@ extern "C" adafac_status adafac_residual_norm_static(int dim, int depth, double 
   for (int j = 0; j < dim; ++j) V *= n + 1;
   const long long nblocks = (V + kVertsPerBlock - 1) / kVertsPerBlock;
   if (nblocks > kMaxPartials) return ADAFAC_ERR_INVALID_ARG;  // beyond the scratch
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return ADAFAC_ERR_CUDA;
-  double* partials = scratch_address(dev);
-  if (!partials) return ADAFAC_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* partials = scratch_address(s);
+  if (!partials) return ADAFAC_ERR_CUDA;
   const double h = 1.0 / (double)n;
   const double hfac = dim == 2 ? 1.0 : h;
   const double hD = dim == 2 ? h * h : h * h * h;

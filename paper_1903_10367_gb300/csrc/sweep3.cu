@@ -34,6 +34,8 @@
 //     (the support of the restriction) in shared memory, and accumulate the
 //     restriction and the damping right-hand side of their coarse columns as
 //     the planes pass.
+#include <algorithm>
+
 #include "common.cuh"
 #include "mbarrier.cuh"
 #include "sweep3.cuh"
@@ -263,7 +265,9 @@ __global__ void __launch_bounds__(NT, MINB)
     if (s_fail) break;
     if (tid == 0 && t + PREF < t1) issue(t + PREF);
     const int k = (t - t0) % NSTAGE;
-    if (!mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
+    if (!mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1, p.wait_polls)) {
+      // the slot's data may not have landed: nothing of this step is stored,
+      // and the block leaves at the next barrier
       s_fail = t - t0 + 1;
       if (atomicCAS(p.fault, 0, 1) == 0) {  // the first failure records where
         p.fault_info[0] = MODE;
@@ -275,6 +279,7 @@ __global__ void __launch_bounds__(NT, MINB)
         p.fault_info[6] = tid;
         p.fault_info[7] = t1 - t0;
       }
+      continue;
     }
     const float* sE = smem + k * 2 * PLANE_F;
     const float* sRhs = sE + PLANE_F;
@@ -458,7 +463,8 @@ __global__ void __launch_bounds__(UNT, 3)
     if (s_fail) break;
     if (tid == 0 && t + PREF < t1) issue(t + PREF);
     const int k = (t - t0) % NSTAGE;
-    if (t < t1 && !mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1)) {
+    if (t < t1 && !mbar_wait(bar0 + 8 * k, ((t - t0) / NSTAGE) & 1, p.wait_polls)) {
+      // as in the down-pass: no store of this step, leave at the next barrier
       s_fail = t - t0 + 1;
       if (atomicCAS(p.fault, 0, 1) == 0) {
         p.fault_info[0] = 10 + MODE;
@@ -470,6 +476,7 @@ __global__ void __launch_bounds__(UNT, 3)
         p.fault_info[6] = tid;
         p.fault_info[7] = t1 - t0;
       }
+      continue;
     }
     const float* sE = smem + k * 2 * UPLANE_F;
     const float* sRhs = sE + UPLANE_F;

@@ -43,6 +43,7 @@ struct Sweep3Params {
   int* applied = nullptr;          // &ctl->applied
   int* fault = nullptr;            // &ctl->fault: set when a bounded wait gives up
   int* fault_info = nullptr;       // &ctl->fault_info[0]
+  long long wait_polls = 1LL << 22;  // polls of a staged-plane wait before it gives up
 };
 
 // The refinement residual of the uniform 3-D operator A = alpha [32, 0, -2, -1]

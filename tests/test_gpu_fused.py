@@ -60,6 +60,46 @@ def test_fused_equals_levelwise_and_oracle(L, variant, k):
     b.close()
 
 
+@pytest.fixture(scope="module")
+def depth5_steps():
+    """Two FP64 oracle cycles of the 3-D depth-5 workload (243^3 cells) from a
+    random initial iterate, with the level vectors of each cycle."""
+    f = wl.get("poisson3d_d5").f()
+    H = oc.build_hierarchy(3, 5, np.array([1.0]), True, f)
+    u0 = wl.random_vertex_field(3, 5, 23)
+    steps = {}
+    u = u0
+    for k in (1, 2):
+        u, parts = oc.cycle(H, u, return_parts=True)
+        steps[k] = (u - u0, parts)
+    return f, u0, steps
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_fused_step_at_depth5_matches_the_oracle_step_by_step(depth5_steps, k):
+    # Only at depth 5 do the fused sweeps run with all their tile seams: the
+    # up-pass has two x-tiles of 41 coarse columns (the restriction and
+    # damping windows of coarse columns 40 and 41 straddle their seam) and
+    # the down-pass four 64-column tiles.  One refinement step of k FP32 cycles
+    # from a random iterate must give the correction of k FP64 oracle cycles,
+    # and the level vectors of the step's last cycle those of the oracle's
+    # k-th cycle: r_l, b~_l = omega S~^T r_{l+1} and g_l = c_l - c~_l.
+    f, u0, steps = depth5_steps
+    want, parts = steps[k]
+    S = adafac.Solver(3, 5, 1.0, f, adafac.default_options(precision="mixed", inner_cycles=k))
+    S.set_solution(u0)
+    S.cycle(k)
+    got = S.solution() - u0
+    fields = {(name, l): S.field(name, l) for l in range(1, 5) for name in ("r", "bt", "g")}
+    S.close()
+    assert _rel(got, want) < FP32_RTOL
+    for l in range(1, 5):
+        g_want = parts["c"][l] - parts["ct"][l]
+        for name, w in (("r", parts["r"][l]), ("bt", parts["bt"][l]), ("g", g_want)):
+            a = fields[(name, l)].reshape(w.shape)
+            assert _rel(a, w) < FP32_RTOL, (name, l, _rel(a, w))
+
+
 def test_fused_counts_cycles_and_converges_like_levelwise():
     res = {}
     for path in ("auto", "levelwise"):

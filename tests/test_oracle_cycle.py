@@ -122,10 +122,30 @@ def _rtilde_truncated_2d_dense(n_c):
     return Rt
 
 
+def _rtilde_truncated_dense(d, n_c):
+    """R~ / omega from brute-force matrices of the eps = 1 problem on the level
+    of n_f = 3 n_c cells: S = D^-1 A P (A from the global hats, P from the
+    coarse hats evaluated at the fine vertices), kept where the fine vertex
+    lies within two fine cells of 3J in every direction (the 5^d support of
+    P), and transposed: row J restricts the fine residual to coarse vertex J."""
+    n_f = 3 * n_c
+    fin = _brute.interior_mask(d, n_f)
+    cin = _brute.interior_mask(d, n_c)
+    A = _brute.stiffness_dense(d, n_f, 1.0)[np.ix_(fin, fin)]
+    P = _brute.dlinear_prolongation_dense(d, n_c)[np.ix_(fin, cin)]
+    S = (A @ P) / np.diag(A)[:, None]
+    fpos = np.indices((n_f + 1,) * d).reshape(d, -1).T[fin]
+    cpos = np.indices((n_c + 1,) * d).reshape(d, -1).T[cin]
+    dist = np.abs(fpos[:, None, :] - 3 * cpos[None, :, :]).max(axis=2)
+    S[dist > 2] = 0.0
+    return S.T
+
+
 @pytest.mark.parametrize("d,L,variant,rtilde,lmin", [
     (2, 2, "jac", "truncated", 1), (2, 3, "jac", "truncated", 1), (2, 3, "jac", "exact", 1),
     (2, 3, "additive", "truncated", 1), (2, 3, "pi", "truncated", 1),
     (2, 3, "exp", "truncated", 1), (3, 2, "jac", "exact", 1), (3, 2, "pi", "exact", 1),
+    (3, 2, "jac", "truncated", 1),
     (2, 3, "jac", "truncated", 2), (2, 3, "pi", "truncated", 2), (2, 3, "jac", "exact", 3)])
 def test_cycle_equals_dense_restatement_of_eq9(d, L, variant, rtilde, lmin):
     rng = np.random.default_rng(12)
@@ -157,8 +177,10 @@ def test_cycle_equals_dense_restatement_of_eq9(d, L, variant, rtilde, lmin):
         for l in range(lmin + 1, L + 1):
             if rtilde == "exact":
                 Rt = w * Pm[l].T @ A[l] @ np.linalg.inv(D[l])
-            else:
+            elif d == 2:
                 Rt = w * _rtilde_truncated_2d_dense(3 ** (l - 1))
+            else:
+                Rt = w * _rtilde_truncated_dense(d, 3 ** (l - 1))
             M -= Pchain(l - 1) @ (wt * np.linalg.inv(D[l - 1])) @ Rt @ Pchain(l).T
     if variant == "pi":
         for l in range(lmin + 1, L + 1):
