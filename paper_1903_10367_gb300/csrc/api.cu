@@ -23,7 +23,6 @@ namespace {
 
 constexpr int kHistCap = 8192;
 constexpr int kNormBlocks = 152 * 8;
-constexpr int kRefineZC = 16;    // fine planes per block of the 3-D refinement residual
 // coarse grids up to this many vertices take the warp-per-vertex restriction
 // in the mixed cycles: there a thread per coarse vertex leaves most of the
 // GPU idle and each thread's 5^d window is a long dependent chain
@@ -98,7 +97,7 @@ struct adafac_handle_s {
   bool fast3 = false;
   float* e32b = nullptr;     // second correction buffer (ping-pong)
   int ebase = 0;             // which of e32 / e32b holds zeros at a step start
-  double* bq = nullptr;      // b / alpha (3-D uniform path)
+  double* bq = nullptr;      // b / alpha (3-D uniform path; fixed point after setup)
   double* ub = nullptr;      // Dirichlet values on the boundary, zero inside
   long long e_elems = 0;     // floats of e32 / e32b / rhs32 (padded rows on the 3-D path)
   int npartials = 0;
@@ -262,7 +261,9 @@ void carve(adafac_handle h, Carver& cv) {
   // one norm partial per block of the refinement residual in use (the fused
   // path may still fall back to the level kernels at setup)
   h->npartials = kNormBlocks;
-  if (h->fast3) h->npartials = std::max(h->npartials, refine3_blocks(h->lev[L].n, kRefineZC));
+  if (h->fast3)
+    h->npartials =
+        std::max(h->npartials, refine3_blocks(h->lev[L].n, refine3_zc(h->lev[L].n)));
   if (mixed)
     h->npartials = std::max(h->npartials, D == 2 ? residual_g_blocks<2>(h->lev[L].n)
                                                  : residual_g_blocks<3>(h->lev[L].n));
@@ -504,7 +505,7 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     Refine3Params& rf = h->rf;
     rf = Refine3Params();
     rf.n = fine.n;
-    rf.zc = kRefineZC;
+    rf.zc = refine3_zc(fine.n);
     rf.ldx = h->ldx;
     // A = alpha [32, 0, -2, -1]: the refinement residual sums the integer
     // stencil exactly (checked to the last bits of the assembled coefficients)
@@ -512,9 +513,12 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     const bool integer_stencil =
         rf.alpha > 0.0 && std::fabs(a.cst[13] - 32.0 * rf.alpha) <= 1e-14 * a.cst[13] &&
         std::fabs(a.cst[9] + 2.0 * rf.alpha) <= 1e-14 * rf.alpha;
+    int ealpha = 0;
+    rf.malpha = (float)std::frexp(rf.alpha, &ealpha);
+    rf.ealpha = ealpha;
     rf.hD = std::pow(1.0 / fine.n, 3);
     rf.u = h->u;
-    rf.bq = h->bq;
+    rf.bq = reinterpret_cast<const long long*>(h->bq);
     rf.rhs32 = h->rhs32;
     rf.partials = h->partials;
     rf.ctl = h->ctl;
@@ -536,6 +540,7 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     // b / alpha and its largest exponent, for the fixed-point refinement residual
     launch_scale(h->b, h->bq, fine.V, 1.0 / h->rf.alpha, s);
     launch_max_exponent(h->bq, fine.V, &h->ctl->bexp, nullptr, s);
+    launch_fix_scaled(reinterpret_cast<long long*>(h->bq), fine.V, h->ctl, s);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda(h, "setup");
   return check_cuda(h, "setup");
@@ -747,7 +752,7 @@ int fast3_step(adafac_handle h, int k, int ebase) {
   cudaMemsetAsync(&h->ctl->uexp, 0, sizeof(int), s);
   launch_max_exponent(h->u, h->lev[L].V, &h->ctl->uexp, h->ctl, s);
   timed(h, ADAFAC_KERNEL_REFINE, [&] { launch_refine3(rf, s); });
-  launch_norm_finalize(h->partials, refine3_blocks(h->lev[L].n, kRefineZC), h->ctl, h->hist,
+  launch_norm_finalize(h->partials, refine3_blocks(h->lev[L].n, rf.zc), h->ctl, h->hist,
                        kHistCap, 0, s);
   h->launches += 3;
   Sweep3Params p = h->sw;

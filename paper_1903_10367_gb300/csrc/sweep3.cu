@@ -602,27 +602,42 @@ __global__ void __launch_bounds__(UNT, 3)
 //
 // The d-linear stencil in 3-D is alpha [32, 0, -2, -1] (centre, faces, edges,
 // corners; alpha = eps h / 12), so A u = alpha S u with integer weights.  u and
-// b / alpha are converted to 64-bit fixed point with a common scale 2^F that
-// keeps every value below 2^56, and S u and b / alpha - S u are summed exactly
-// in integers: the only rounding is the conversion of each value (below
-// 2^-F, i.e. 2^-55 of the largest magnitude) and of the result to FP32.  This
-// is at least as accurate as FP64 arithmetic and runs on the integer units;
-// the GPU's FP64 rate (about 1/64 of FP32) would otherwise bound the kernel.
-// Per plane p, W_p = 32 u - 2 D_p and Y_p = -(2 X_p + D_p), with X_p / D_p the
-// sums of the 4 in-plane face / diagonal neighbours; (S u)_s = W_s + Y_{s-1} +
-// Y_{s+1}.
-constexpr int RT_X = 32, RT_Y = 8;
+// b / alpha are taken to 64-bit fixed point with a common scale 2^F that keeps
+// every value below 2^56, and S u and b / alpha - S u are summed exactly in
+// integers: the only rounding is the conversion of each value (below 2^-F,
+// i.e. 2^-55 of the largest magnitude) and of the result to FP32.  This is at
+// least as accurate as FP64 arithmetic and runs on the integer units; the
+// GPU's FP64 rate (about 1/64 of FP32) would otherwise bound the kernel.
+// b / alpha is stored in fixed point at setup (scale 2^(1078 - bexp)) and only
+// shifted to the step's scale here.
+//
+// A block owns 32 columns x 16 rows and zc planes; a warp owns a strip of 4
+// rows, a lane one column.  Per plane the block converts the plane's 34 x 18
+// box of u (the tile and its ring) to fixed point into one of two shared
+// buffers; one barrier per plane orders the hand-over.  The values of plane
+// z + 1 and b of plane z are loaded into registers while plane z is worked on,
+// so the global loads of one plane overlap the arithmetic of the previous.
+// Per plane p, W_p = 32 u - 2 D_p and Y_p = -(2 X_p + D_p), with X_p / D_p
+// the sums of the 4 in-plane face / diagonal neighbours; (S u)_s = W_s +
+// Y_{s-1} + Y_{s+1}.  In a row, with h = u(x-1) + u(x+1) and m = u(x):
+// X = h + m(y-1) + m(y+1) and D = h(y-1) + h(y+1).
+constexpr int RT_X = 32, RT_Y = 16, RT_RB = 4;
+constexpr int RT_NT = RT_X * (RT_Y / RT_RB);                  // 128 threads
+constexpr int RT_W = RT_X + 2, RT_H = RT_Y + 2;               // staged box 34 x 18
+constexpr int RT_NH = (RT_W * RT_H + RT_NT - 1) / RT_NT;      // box values per thread
+constexpr int RT_MINB = 6;                                    // resident blocks per SM
+static_assert(RT_Y % RT_RB == 0 && RT_NT % 32 == 0, "refinement tiling");
 
-// x * 2^F as an integer, F = 1078 - emax (emax >= the biased exponent of x);
-// values below 2^-1022 count as zero
+// x 2^F as an integer, F = 1078 - emax (emax >= the biased exponent of x);
+// values below 2^-1022 count as zero.  (m << 3) >> (emax - e) is m 2^(e - emax
+// + 3): exact when e >= emax - 3, truncated towards zero below.
 __device__ __forceinline__ long long to_fixed(double x, int emax) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const long long bits = __double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7ff);
-  if (e == 0) return 0;
-  const long long m = (long long)((bits & 0xfffffffffffffull) | 0x10000000000000ull);
-  const int sh = e - emax + 3;  // <= 3: |result| < 2^56
-  const long long v = sh >= 0 ? (m << sh) : (sh > -63 ? (m >> -sh) : 0);
-  return (bits >> 63) ? -v : v;
+  const long long m = ((bits & 0xfffffffffffffLL) | 0x10000000000000LL) << 3;  // < 2^56
+  const int k = emax - e;
+  const long long v = (e != 0 && k >= 0 && k < 64) ? (m >> k) : 0;
+  return bits < 0 ? -v : v;
 }
 
 // |R| < 2^63 as a float, without cancellation
@@ -633,50 +648,104 @@ __device__ __forceinline__ float fixed_to_float(long long R) {
   return R < 0 ? -f : f;
 }
 
-__global__ void __launch_bounds__(RT_X* RT_Y) k_refine3(const Refine3Params p) {
+__global__ void __launch_bounds__(RT_NT, RT_MINB) k_refine3(const Refine3Params p) {
   if (halted(p.ctl)) return;
-  __shared__ long long sU[(RT_X + 2) * (RT_Y + 2)];
-  __shared__ double red[RT_X * RT_Y / 32];
-  const int emax = max(max(p.ctl->uexp, p.ctl->bexp), 1);
+  __shared__ long long sU[2][RT_W * RT_H];
+  __shared__ double red[RT_NT / 32];
+  const int bexp = max(p.ctl->bexp, 1);
+  const int emax = max(p.ctl->uexp, bexp);
   const int F = 1078 - emax;
-  int ealpha;
-  const float malpha = (float)frexp(p.alpha, &ealpha);  // alpha = malpha 2^ealpha
+  const int bsh = min(emax - bexp, 63);                // b / alpha: scale 2^(1078 - bexp)
+  // rhs = alpha R 2^-F = (R malpha) 2^ks; one multiplication when 2^ks is a
+  // normal float (the same rounded value as ldexpf)
+  const int ks = p.ealpha - F;
+  const bool one_mul = ks >= -126 && ks <= 127;
+  const float sc = one_mul ? ldexpf(p.malpha, ks) : 0.f;
   const int n = p.n, np1 = n + 1;
-  const int tx = threadIdx.x % RT_X, ty = threadIdx.x / RT_X;
-  const int x = blockIdx.x * RT_X + tx, y = blockIdx.y * RT_Y + ty;
+  const long long plane = (long long)np1 * np1;
+  const int tx = threadIdx.x & 31, strip = threadIdx.x >> 5;
+  const int x = blockIdx.x * RT_X + tx;
+  const int y0 = blockIdx.y * RT_Y + strip * RT_RB;
   const int zlo = blockIdx.z * p.zc + 1;
-  const int zhi = min(zlo + p.zc, n);            // planes [zlo, zhi)
-  const bool inner = x >= 1 && x <= n - 1 && y >= 1 && y <= n - 1;
-  constexpr int W = RT_X + 2;
-  long long Wm = 0, Ym = 0, Ymm = 0;             // W_{z-1}, Y_{z-1}, Y_{z-2}
-  float acc = 0.f;                               // sum of (R 2^-32)^2
-  for (int z = zlo - 1; z <= zhi; ++z) {
-    for (int i = threadIdx.x; i < W * (RT_Y + 2); i += RT_X * RT_Y) {
-      const int xx = blockIdx.x * RT_X - 1 + i % W, yy = blockIdx.y * RT_Y - 1 + i / W;
-      long long v = 0;
-      if (xx >= 0 && xx <= n && yy >= 0 && yy <= n && z >= 0 && z <= n)
-        v = to_fixed(p.u[((long long)z * np1 + yy) * np1 + xx], emax);
-      sU[i] = v;
+  const int zhi = min(zlo + p.zc, n);                  // residual planes [zlo, zhi)
+  const bool xin = x >= 1 && x <= n - 1;
+  // the box values this thread converts: box index i = tid + k NT, at plane
+  // offset hoff (-1: outside the box or the grid)
+  int hoff[RT_NH];
+#pragma unroll
+  for (int k = 0; k < RT_NH; ++k) {
+    const int i = threadIdx.x + k * RT_NT;
+    const int xx = blockIdx.x * RT_X - 1 + i % RT_W, yy = blockIdx.y * RT_Y - 1 + i / RT_W;
+    const bool ok = i < RT_W * RT_H && xx >= 0 && xx <= n && yy >= 0 && yy <= n;
+    hoff[k] = ok ? yy * np1 + xx : -1;
+  }
+  bool yin[RT_RB];
+#pragma unroll
+  for (int i = 0; i < RT_RB; ++i) yin[i] = xin && y0 + i >= 1 && y0 + i <= n - 1;
+  double un[RT_NH];
+  long long bn[RT_RB];
+  auto fetch_u = [&](int z) {  // z in [0, n]
+    const double* up = p.u + (long long)z * plane;
+#pragma unroll
+    for (int k = 0; k < RT_NH; ++k) un[k] = hoff[k] >= 0 ? up[hoff[k]] : 0.0;
+  };
+  auto fetch_b = [&](int z) {
+    const bool zin = z >= zlo && z < zhi;
+    const long long* bp = p.bq + (long long)z * plane + (long long)y0 * np1 + x;
+#pragma unroll
+    for (int i = 0; i < RT_RB; ++i) bn[i] = zin && yin[i] ? bp[(long long)i * np1] : 0;
+  };
+  fetch_u(zlo - 1);
+#pragma unroll
+  for (int i = 0; i < RT_RB; ++i) bn[i] = 0;
+  long long P[RT_RB], Ym[RT_RB];  // W_{z-1} + Y_{z-2} and Y_{z-1} per row
+#pragma unroll
+  for (int i = 0; i < RT_RB; ++i) P[i] = Ym[i] = 0;
+  float acc = 0.f;                // sum of (R 2^-32)^2
+  int buf = 0;
+  for (int z = zlo - 1; z <= zhi; ++z, buf ^= 1) {
+    // plane z (loaded during the previous plane) into the shared buffer, then
+    // the loads of plane z + 1 and of b of plane z go out
+    long long* S = sU[buf];
+#pragma unroll
+    for (int k = 0; k < RT_NH; ++k) {
+      const int i = threadIdx.x + k * RT_NT;
+      if (i < RT_W * RT_H) S[i] = to_fixed(un[k], emax);
     }
+    if (z + 1 <= zhi) fetch_u(z + 1);
+    long long bc[RT_RB];          // b of plane z - 1
+#pragma unroll
+    for (int i = 0; i < RT_RB; ++i) bc[i] = bn[i];
+    fetch_b(z);
     __syncthreads();
-    const int ai = (ty + 1) * W + tx + 1;
-    const long long X = (sU[ai - 1] + sU[ai + 1]) + (sU[ai - W] + sU[ai + W]);
-    const long long D = (sU[ai - W - 1] + sU[ai - W + 1]) + (sU[ai + W - 1] + sU[ai + W + 1]);
-    const long long Wz = sU[ai] * 32 - D * 2;
-    const long long Yz = -(X * 2 + D);
-    __syncthreads();
-    const int zz = z - 1;  // residual plane
-    if (zz >= zlo && zz < zhi && inner) {
-      const long long gi = ((long long)zz * np1 + y) * np1 + x;
-      const long long R = to_fixed(p.bq[gi], emax) - ((Wm + Ymm) + Yz);
-      const float Rf = fixed_to_float(R);
-      p.rhs32[((long long)zz * np1 + y) * p.ldx + x] = ldexpf(Rf * malpha, ealpha - F);
-      const float Rs = Rf * 2.3283064365386963e-10f;  // 2^-32
-      acc = fmaf(Rs, Rs, acc);
+    const int zr = z - 1;  // residual plane
+    const bool zout = zr >= zlo && zr < zhi;
+    const long long* c = S + strip * RT_RB * RT_W + tx;  // box row of y0 - 1, column x - 1
+    long long hU = c[0] + c[2], mU = c[1];
+    long long hC = c[RT_W] + c[RT_W + 2], mC = c[RT_W + 1];
+    float* rrow = p.rhs32 + ((long long)zr * np1 + y0) * p.ldx + x;
+#pragma unroll
+    for (int i = 0; i < RT_RB; ++i) {
+      const long long* d = c + (i + 2) * RT_W;
+      const long long hD = d[0] + d[2], mD = d[1];
+      const long long X = hC + (mU + mD);
+      const long long D = hU + hD;
+      const long long W = mC * 32 - D * 2;
+      const long long Y = -(X * 2 + D);
+      if (zout && yin[i]) {
+        const long long R = (bc[i] >> bsh) - (P[i] + Y);
+        const float Rf = fixed_to_float(R);
+        rrow[(long long)i * p.ldx] = one_mul ? Rf * sc : ldexpf(Rf * p.malpha, ks);
+        const float Rs = Rf * 2.3283064365386963e-10f;  // 2^-32
+        acc = fmaf(Rs, Rs, acc);
+      }
+      P[i] = W + Ym[i];
+      Ym[i] = Y;
+      hU = hC;
+      mU = mC;
+      hC = hD;
+      mC = mD;
     }
-    Ymm = Ym;
-    Ym = Yz;
-    Wm = Wz;
   }
   // block sum: warp shuffles, then the warps' partial sums
   double dacc = (double)acc;
@@ -686,11 +755,19 @@ __global__ void __launch_bounds__(RT_X* RT_Y) k_refine3(const Refine3Params p) {
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < RT_X * RT_Y / 32; ++w) t += red[w];
-    const double sc = ldexp(p.alpha, 32 - F);  // r = sc R 2^-32
+    for (int w = 0; w < RT_NT / 32; ++w) t += red[w];
+    const double scd = ldexp(p.alpha, 32 - F);  // r = scd R 2^-32
     const int b = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    p.partials[b] = t * sc * sc * p.hD;
+    p.partials[b] = t * scd * scd * p.hD;
   }
+}
+
+// b / alpha in place as 64-bit fixed point with scale 2^(1078 - max(bexp, 1))
+__global__ void k_fix_scaled(long long* __restrict__ bq, long long V, const Control* ctl) {
+  const int emax = max(ctl->bexp, 1);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V;
+       i += (long long)gridDim.x * blockDim.x)
+    bq[i] = to_fixed(__longlong_as_double(bq[i]), emax);
 }
 
 __global__ void k_max_exponent(const double* __restrict__ x, long long V, int* out,
@@ -799,10 +876,32 @@ void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int m
   }
 }
 
+void refine3_grid(int n, int zc, dim3* grid) {
+  // columns and rows 1 .. n - 1 carry residuals
+  *grid = dim3((n + RT_X - 1) / RT_X, (n + RT_Y - 1) / RT_Y, (n - 1 + zc - 1) / zc);
+}
+
 int refine3_blocks(int n, int zc) {
-  const int gx = (n + 1 + RT_X - 1) / RT_X, gy = (n + 1 + RT_Y - 1) / RT_Y;
-  const int gz = (n - 1 + zc - 1) / zc;
-  return gx * gy * gz;
+  dim3 g;
+  refine3_grid(n, zc, &g);
+  return (int)(g.x * g.y * g.z);
+}
+
+int refine3_zc(int n) {
+  // one wave of RT_MINB resident blocks on each of the 152 SMs of a GB300: the
+  // planes split into as many slabs as that allows.  The rule does not query
+  // the device, so the workspace layout (one norm partial per block) is the
+  // same wherever it is computed.
+  constexpr long long kSlots = 152 * RT_MINB;
+  dim3 g;
+  refine3_grid(n, 1, &g);
+  const long long tiles = (long long)g.x * g.y;
+  const long long slabs = std::max(1LL, kSlots / tiles);
+  return (int)std::max(1LL, (n - 1 + slabs - 1) / slabs);
+}
+
+void launch_fix_scaled(long long* bq, long long V, const Control* ctl, cudaStream_t s) {
+  k_fix_scaled<<<152 * 8, 256, 0, s>>>(bq, V, ctl);
 }
 
 void launch_max_exponent(const double* x, long long V, int* out, const Control* ctl,
@@ -815,9 +914,9 @@ void launch_scale(const double* b, double* bq, long long V, double inv_alpha, cu
 }
 
 void launch_refine3(const Refine3Params& p, cudaStream_t s) {
-  const int n = p.n;
-  dim3 grid((n + 1 + RT_X - 1) / RT_X, (n + 1 + RT_Y - 1) / RT_Y, (n - 1 + p.zc - 1) / p.zc);
-  k_refine3<<<grid, RT_X * RT_Y, 0, s>>>(p);
+  dim3 grid;
+  refine3_grid(p.n, p.zc, &grid);
+  k_refine3<<<grid, RT_NT, 0, s>>>(p);
 }
 
 }  // namespace adafac

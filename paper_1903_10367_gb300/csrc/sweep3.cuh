@@ -52,9 +52,11 @@ struct Sweep3Params {
 struct Refine3Params {
   int n = 0, zc = 0, ldx = 0;
   double alpha = 0;                // eps h / 12
+  float malpha = 0;                // alpha = malpha 2^ealpha, malpha in [0.5, 1)
+  int ealpha = 0;
   double hD = 0;
   const double* u = nullptr;
-  const double* bq = nullptr;      // b / alpha
+  const long long* bq = nullptr;   // b / alpha in fixed point, scale 2^(1078 - max(bexp, 1))
   float* rhs32 = nullptr;          // padded FP32 layout (row stride ldx)
   double* partials = nullptr;
   const Control* ctl = nullptr;    // uexp, bexp: exponents fixing the scale
@@ -77,7 +79,12 @@ void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int m
 void sweep3_grid(int nc, int zc, dim3* grid);       // up-passes (41 x 4 coarse columns)
 void sweep3_grid_down(int nc, int zc, dim3* grid);  // down-passes (64-column tiles)
 int refine3_blocks(int n, int zc);
+// planes per block of the refinement residual (one wave of resident blocks)
+int refine3_zc(int n);
 void launch_refine3(const Refine3Params& p, cudaStream_t s);
+// b / alpha (FP64, in place) to the fixed point of Refine3Params::bq, after
+// the largest exponent ctl->bexp has been found
+void launch_fix_scaled(long long* bq, long long V, const Control* ctl, cudaStream_t s);
 // One restriction (level l + 1 -> l) or prolongation (l - 1 -> l) of the 3-D
 // uniform path's coarse levels, with the d-linear weights as constants: n_c /
 // n_f are the coarse / fine cell counts.
