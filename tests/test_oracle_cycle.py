@@ -366,3 +366,79 @@ def test_rediscretised_equals_galerkin_when_eps_is_constant_on_coarse_cells(d):
 
         np.testing.assert_allclose(dense(Hr.levels[l].op), dense(Hg.levels[l].op),
                                    rtol=1e-12, atol=1e-13)
+
+
+def _vcycle(H, l, u, b, nu=2, w=0.6):
+    """A multiplicative V(nu, nu)-cycle with damped Jacobi smoothing on the
+    same hierarchy (the textbook scheme, for comparison only): pre-smoothing,
+    coarse correction P (cycle on R r), post-smoothing; exact solve on level 1."""
+    lev = H.levels[l]
+    d = H.d
+
+    def jacobi(u):
+        r = fem.zero_boundary(b - lev.op.apply(u))
+        return u + cycle.jacobi_correction(H, l, r, w)
+
+    if l == 1:
+        n = lev.n
+        N = (n + 1) ** d
+        M = np.zeros((N, N))
+        for k in range(N):
+            e = np.zeros(N)
+            e[k] = 1.0
+            M[:, k] = lev.op.apply(e.reshape((n + 1,) * d)).ravel()
+        inn = _brute.interior_mask(d, n)
+        x = np.zeros(N)
+        x[inn] = np.linalg.solve(M[np.ix_(inn, inn)], b.ravel()[inn])
+        return x.reshape(b.shape)
+    for _ in range(nu):
+        u = jacobi(u)
+    rc = cycle.R(H, l, fem.zero_boundary(b - lev.op.apply(u)))
+    u = u + cycle.P(H, l, _vcycle(H, l - 1, np.zeros_like(rc), rc, nu, w))
+    for _ in range(nu):
+        u = jacobi(u)
+    return u
+
+
+def _cycles_to(H, step, tol=1e-8, cap=2000):
+    u = np.zeros_like(H.b)
+    r0 = cycle.residual_norm(H, cycle.residual(H, H.L, u, H.b))
+    for c in range(1, cap + 1):
+        u = step(u)
+        if cycle.residual_norm(H, cycle.residual(H, H.L, u, H.b)) / r0 <= tol:
+            return c
+    return cap
+
+
+def test_slow_convergence_on_fine_blocks_is_a_property_of_the_geometric_hierarchy():
+    # Sec. 2.4 and Sec. 5: BoxMG transfers restore the Poisson convergence for
+    # jumps that the coarse levels can represent, and no cycle on the same
+    # hierarchy does better when the blocks are finer than the coarse cells.
+    # 2-D depth 3, f = 1, eps in {1, 1e-2}; counts to 1e-8 from u = 0.
+    d, L, n = 2, 3, 27
+    f = wl.constant_rhs(d, L)
+
+    def counts(eps, kind):
+        H = cycle.build_hierarchy(d, L, eps, False, f, kind)
+        return (_cycles_to(H, lambda u: cycle.cycle(H, u, variant="jac")),
+                _cycles_to(H, lambda u: _vcycle(H, L, u, H.b), cap=400))
+
+    jac0, v0 = counts(np.ones((n, n)), "dlinear")
+    rng = np.random.Generator(np.random.PCG64(1903))
+    cols = np.broadcast_to(np.repeat(rng.choice([1.0, 1e-2], size=9), 3)[:, None], (n, n))
+    # eps varying along x in columns of 3 cells: BoxMG interpolation is the
+    # exact 1-D one, d-linear is not
+    jb, vb = counts(cols.copy(), "boxmg")
+    jd, vd = counts(cols.copy(), "dlinear")
+    assert jb <= 1.15 * jac0 and vb <= 1.2 * v0, (jb, vb, jac0, v0)
+    assert jd >= 2 * jac0 and vd >= 2 * v0, (jd, vd)
+    # random blocks of level-1 cells: every level resolves them
+    for kind in ("dlinear", "boxmg"):
+        j, _ = counts(wl.eps_random_blocks(d, L, 9, 1e-2, 1903), kind)
+        assert j <= 1.3 * jac0, (kind, j, jac0)
+    # random blocks of level-2 cells, finer than the level-1 cells: the
+    # multiplicative cycle slows by the same factor as adAFAC-Jac, so the
+    # slowdown belongs to the coarse spaces, not to the additive method
+    j, v = counts(wl.eps_random_blocks(d, L, 3, 1e-2, 1903), "boxmg")
+    assert j >= 4 * jac0 and v >= 4 * v0, (j, v, jac0, v0)
+    assert abs((j / jac0) / (v / v0) - 1.0) <= 0.3, (j / jac0, v / v0)
