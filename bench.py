@@ -12,8 +12,8 @@ ms_per_step is the time to 1e-8.
 
 Under torchrun every rank solves its own replica (the method needs no
 exchange between independent solves): weak scaling, max time over ranks.
-``--impl reference`` times the CPU FP64 oracle (rank 0 only) on a bounded
-sample of the same workload.
+``--impl reference`` times the CPU FP64 oracle (rank 0 only) on the same
+workload: one oracle cycle per step, the steps spread over the host cores.
 """
 import os
 
@@ -144,16 +144,42 @@ def _algorithmic_bytes(kind, w, precision, eps_scalar):
     return int(round(per[kind] * N))
 
 
-def run_oracle_sample(w, seconds: float):
-    """Times the FP64 oracle's adAFAC-Jac cycles on a bounded sample of the
-    workload: the same problem on a tree one level shallower (1/3^d of the
-    fine grid), as many cycles as fit in ``seconds``."""
+def _host_cpu():
+    """Cores this process may run on (nproc) and the CPU model (lscpu)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name":
+                model = val.strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def _oracle_hierarchy(w):
+    """The oracle's level hierarchy of the workload (FP64 setup, untimed)."""
     from oracle import cycle as oc
-    ws = w.with_depth(max(1, w.depth - 1))
-    eps, sc = ws.eps()
-    H = oc.build_hierarchy(ws.dim, ws.depth, eps, sc, ws.f(), ws.transfer)
+    eps, sc = w.eps()
+    t0 = time.perf_counter()
+    H = oc.build_hierarchy(w.dim, w.depth, eps, sc, w.f(), w.transfer)
+    return H, time.perf_counter() - t0
+
+
+def run_oracle_sample(w, seconds: float):
+    """Times the FP64 oracle's adAFAC-Jac cycles on the bench workload itself
+    on one host core: the hierarchy is built untimed, then cycles run from
+    u = 0 until ``seconds`` have passed (at least one)."""
+    from oracle import cycle as oc
+    H, tb = _oracle_hierarchy(w)
     u = np.zeros_like(H.b)
-    upd = sum(ws.level_dofs())
+    upd = sum(w.level_dofs())
     t0 = time.perf_counter()
     n = 0
     while True:
@@ -163,35 +189,62 @@ def run_oracle_sample(w, seconds: float):
             break
     dt = time.perf_counter() - t0
     return {"value": n * upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 adAFAC-Jac cycles of {ws.name} (dim {ws.dim}, depth {ws.depth}: "
-                      f"the workload one level shallower), numpy on 1 host core, {dt:.1f} s"}
+            "sample": f"{n} FP64 adAFAC-Jac cycle(s) of {w.name} (the bench workload, dim "
+                      f"{w.dim}, depth {w.depth}) from u = 0, numpy on 1 host core, {dt:.1f} s; "
+                      f"hierarchy setup {tb:.1f} s untimed"}
+
+
+# hierarchy shared by the forked workers of the reference arm
+_POOL_H = None
+
+
+def _oracle_step(_):
+    from oracle import cycle as oc
+    oc.cycle(_POOL_H, np.zeros_like(_POOL_H.b))
+    return 0
 
 
 def bench_reference(args, w):
+    """The reference arm: the FP64 oracle on the bench workload, on all host
+    cores.  The hierarchy is built once (untimed) and shared with forked
+    worker processes (copy on write; this process never touches a GPU).  A
+    step is one oracle adAFAC-Jac cycle from u = 0; the K timed steps run on
+    P workers at once, so ms_per_step is the wall time of the K steps / K."""
+    global _POOL_H
     ws_, rank, _ = _dist()
     if rank != 0:
         return
-    from oracle import cycle as oc
-    s = w.with_depth(max(1, w.depth - 1))
-    eps, sc = s.eps()
-    H = oc.build_hierarchy(s.dim, s.depth, eps, sc, s.f(), s.transfer)
-    u = np.zeros_like(H.b)
-    for _ in range(args.warmup):
-        u = oc.cycle(H, u)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        u = oc.cycle(H, u)
-    dt = time.perf_counter() - t0
-    upd = sum(s.level_dofs())
+    import multiprocessing as mp
+    H, tb = _oracle_hierarchy(w)
+    cores, model = _host_cpu()
+    # a cycle holds about 16 vertex arrays besides the hierarchy
+    per_task = 16 * 8 * (3 ** w.depth + 1) ** w.dim
+    try:
+        avail = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    except (ValueError, OSError):
+        avail = per_task * cores
+    workers = max(1, min(cores, max(args.steps, 1), int(0.5 * avail // per_task)))
+    _POOL_H = H
+    with mp.get_context("fork").Pool(workers) as pool:
+        if args.warmup:
+            pool.map(_oracle_step, range(args.warmup), chunksize=1)
+        t0 = time.perf_counter()
+        pool.map(_oracle_step, range(args.steps), chunksize=1)
+        dt = time.perf_counter() - t0
+    upd = sum(w.level_dofs())
     value = args.steps * upd / dt
-    sample = (f"one FP64 oracle adAFAC-Jac cycle of {s.name} (the workload one level "
-              f"shallower) per step, numpy on 1 host core")
+    sample = (f"{args.steps} FP64 oracle adAFAC-Jac cycles of {w.name} (the bench workload, "
+              f"dim {w.dim}, depth {w.depth}) from u = 0, one per step, numpy in {workers} "
+              f"forked processes (1 thread each) on {cores} host cores ({model}); hierarchy "
+              f"setup {tb:.1f} s untimed")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": _config(w, args, None),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "config": _config(w, args),
+           "run": {"precision": "fp64", "cycles_per_step": 1, "host_cores": cores,
+                   "host_cpu": model, "workers": workers},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -222,11 +275,12 @@ def _tuning_summary(t):
                 us_tuned=round(t["us_tuned"], 2))
 
 
-def _config(w, args, cycles):
+def _config(w, args):
+    """The workload (the same in both arms): problem, method, tolerance."""
     return {"workload": w.name, "dim": w.dim, "depth": w.depth,
             "fine_dofs": (3 ** w.depth - 1) ** w.dim, "dofs_all_levels": sum(w.level_dofs()),
-            "precision": args.precision, "variant": "adAFAC-Jac", "transfer": w.transfer,
-            "rtilde": "truncated", "tol": args.tol, "cycles_per_step": cycles,
+            "variant": "adAFAC-Jac", "transfer": w.transfer, "rtilde": "truncated",
+            "tol": args.tol,
             "l2": "L2 flushed between steps" if _needs_flush(w, args.precision)
                   else "working set of a step larger than L2",
             "parallelism": f"replicas x{args.gpus}"}
@@ -367,7 +421,9 @@ def bench_ours(args, w):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 cycles + f64 refinement" if args.precision == "mixed" else "f64",
-           "data": "synthetic", "config": dict(_config(w, args, cycles), tuning=_tuning_summary(tuning)),
+           "data": "synthetic", "config": _config(w, args),
+           "run": {"precision": args.precision, "cycles_per_step": cycles,
+                   "tuning": _tuning_summary(tuning)},
            "time_to_tol_ms": ms / args.steps, "e2e": e2e, "gpu_launches": launches,
            "roofline": roofline, "clocks": clk, "cpu_baseline": cpu,
            "fp64_comparator": fp64, "serving": serving}
