@@ -502,6 +502,8 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw.applied = &h->ctl->applied;
     sw.fault = &h->ctl->fault;
     sw.fault_info = &h->ctl->fault_info[0];
+    sw.uexp = &h->ctl->uexp;
+    sw.bdexp = &h->ctl->bdexp;
     Refine3Params& rf = h->rf;
     rf = Refine3Params();
     rf.n = fine.n;
@@ -715,25 +717,33 @@ void coarse_chain32(adafac_handle h) {
   lp.omega_t = cp.omega_tilde;
   for (int k = 0; k < 125; ++k) lp.stilde[k] = cp.stilde[k];
   lp.ctl = h->ctl;
+  auto restrict_to = [&](int l) {  // level l + 1 -> l
+    Level3Params q = lp;
+    q.nc = lv[l].n;
+    q.nf = lv[l + 1].n;
+    q.gscale = cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
+    q.r_f = lv[l + 1].r32;
+    q.r_c = lv[l].r32;
+    q.bt_c = lv[l].bt32;
+    q.g_c = lv[l].g32;
+    q.invd_c = lv[l].invd32;
+    return q;
+  };
+  auto prolong_to = [&](int l) {  // level l - 1 -> l
+    Level3Params q = lp;
+    q.nc = lv[l - 1].n;
+    q.nf = lv[l].n;
+    q.t_c = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
+    q.g_f = lv[l].g32;
+    q.t_f = lv[l].t32;
+    return q;
+  };
   for (int l = L - 2; l >= lmin; --l) {
-    lp.nc = lv[l].n;
-    lp.nf = lv[l + 1].n;
-    lp.gscale = cp.variant == V_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
-    lp.r_f = lv[l + 1].r32;
-    lp.r_c = lv[l].r32;
-    lp.bt_c = lv[l].bt32;
-    lp.g_c = lv[l].g32;
-    lp.invd_c = lv[l].invd32;
-    launch_restrict3u(lp, s);
+    launch_restrict3u(restrict_to(l), s);
     h->launches += 1;
   }
   for (int l = lmin + 1; l <= L - 1; ++l) {
-    lp.nc = lv[l - 1].n;
-    lp.nf = lv[l].n;
-    lp.t_c = l - 1 == lmin ? lv[lmin].g32 : lv[l - 1].t32;
-    lp.g_f = lv[l].g32;
-    lp.t_f = lv[l].t32;
-    launch_prolong3u(lp, s);
+    launch_prolong3u(prolong_to(l), s);
     h->launches += 1;
   }
 }
@@ -748,13 +758,13 @@ int fast3_step(adafac_handle h, int k, int ebase) {
   const int L = h->L;
   cudaStream_t s = h->stream;
   Refine3Params rf = h->rf;
-  // the scale of the fixed-point residual follows the largest |u|
-  cudaMemsetAsync(&h->ctl->uexp, 0, sizeof(int), s);
-  launch_max_exponent(h->u, h->lev[L].V, &h->ctl->uexp, h->ctl, s);
+  // the scale of the fixed-point residual follows the largest |u|: ctl->uexp
+  // is exact here (set by the previous step's last down-pass, or by the call
+  // that set u)
   timed(h, ADAFAC_KERNEL_REFINE, [&] { launch_refine3(rf, s); });
   launch_norm_finalize(h->partials, refine3_blocks(h->lev[L].n, rf.zc), h->ctl, h->hist,
                        kHistCap, 0, s);
-  h->launches += 3;
+  h->launches += 2;
   Sweep3Params p = h->sw;
   const int lmin = h->opt.lmin;
   p.q = L - 1 == lmin ? h->lev[lmin].g32 : h->lev[L - 1].t32;
@@ -921,6 +931,10 @@ adafac_status reset_control(adafac_handle h) {
 }  // namespace
 
 namespace adafac {
+
+// The truncated smoothed-restriction stencil for other parts of the library
+// (the adaptive-tree cycles).
+void smoothed_restriction_stencil(int D, double* out) { smoothed_stencil(D, out); }
 
 // Internal accessors for the request server (same library, not part of the
 // C ABI).
@@ -1323,7 +1337,11 @@ adafac_status adafac_set_solution(adafac_handle h, const double* src, int src_on
                       h->stream) != cudaSuccess)
     return check_cuda(h, "copy iterate");
   k_boundary<<<1024, 256, 0, h->stream>>>(h->u, h->ub, h->lev[h->L].n, h->D, 0);
-  return reset_control(h);
+  adafac_status st = reset_control(h);
+  // the exponent of the new iterate (the scale of the fixed-point residual)
+  if (st == ADAFAC_OK && h->fast3)
+    launch_max_exponent(h->u, h->lev[h->L].V, &h->ctl->uexp, nullptr, h->stream);
+  return st == ADAFAC_OK ? check_cuda(h, "iterate exponent") : st;
 }
 
 adafac_status adafac_set_boundary(adafac_handle h, const double* g, int g_on_device) {
@@ -1339,7 +1357,13 @@ adafac_status adafac_set_boundary(adafac_handle h, const double* g, int g_on_dev
   const int n = h->lev[h->L].n;
   k_boundary<<<1024, 256, 0, h->stream>>>(h->ub, nullptr, n, h->D, 1);
   k_boundary<<<1024, 256, 0, h->stream>>>(h->u, h->ub, n, h->D, 0);
-  return reset_control(h);
+  // the exponents of the Dirichlet values and of the iterate
+  cudaMemsetAsync(&h->ctl->bdexp, 0, sizeof(int), h->stream);
+  launch_max_exponent(h->ub, h->lev[h->L].V, &h->ctl->bdexp, nullptr, h->stream);
+  adafac_status st = reset_control(h);
+  if (st == ADAFAC_OK && h->fast3)
+    launch_max_exponent(h->u, h->lev[h->L].V, &h->ctl->uexp, nullptr, h->stream);
+  return st == ADAFAC_OK ? check_cuda(h, "iterate exponent") : st;
 }
 
 adafac_status adafac_reset(adafac_handle h) {

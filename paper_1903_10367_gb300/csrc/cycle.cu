@@ -384,6 +384,7 @@ __global__ void k_reset_control(Control* ctl) {
   ctl->applied = 0;
   ctl->set_r0 = 1;
   ctl->fault = 0;
+  ctl->uexp = ctl->bdexp;  // u = the Dirichlet values (callers that set u raise it)
 }
 
 __global__ void k_refine_update(double* __restrict__ u, float* __restrict__ e, long long V,

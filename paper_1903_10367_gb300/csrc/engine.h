@@ -62,8 +62,12 @@ struct Control {
   int set_r0;         // 1: the next norm evaluation defines r_0
   int fault;          // 1: a bounded device-side wait gave up (reported as TIMEOUT)
   int fault_info[8];  // where it gave up: mode, block, step index, slot, parity, z
-  int uexp;           // largest biased binary exponent of the fine iterate u
+  int uexp;           // largest biased binary exponent of the fine iterate u (3-D uniform
+                      // path: exact at the start of a refinement step; the step's first
+                      // up-pass resets it to bdexp, its last down-pass raises it to the
+                      // exponents of the u it writes)
   int bexp;           // largest biased binary exponent of b / alpha (3-D uniform path)
+  int bdexp;          // largest biased binary exponent of the Dirichlet values of u
 };
 
 // ---- handle internals used by the request server ---------------------------

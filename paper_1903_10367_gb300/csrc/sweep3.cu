@@ -259,6 +259,12 @@ __global__ void __launch_bounds__(NT, MINB)
   float2 eR[RB], PR[RB], YR[RB];
 #pragma unroll
   for (int i = 0; i < RB; ++i) eR[i] = PR[i] = YR[i] = f2(0.f);
+  // DOWNU: the largest biased exponent of the u this thread writes (the
+  // scale of the next refinement step's fixed-point residual)
+  unsigned uexp_max = 0;
+  auto expo = [](double v) {
+    return (unsigned)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
+  };
 
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
@@ -317,11 +323,15 @@ __global__ void __launch_bounds__(NT, MINB)
         } else {
           const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
           if (mxB.x != 0.f) {
-            p.u[urow + xb] = uo[i][0] + (double)ek.x;
+            const double un = uo[i][0] + (double)ek.x;
+            p.u[urow + xb] = un;
+            uexp_max = max(uexp_max, expo(un));
             eo[0] = 0.f;  // the zero buffer of the next refinement step
           }
           if (mxB.y != 0.f) {
-            p.u[urow + xb + 1] = uo[i][1] + (double)ek.y;
+            const double un = uo[i][1] + (double)ek.y;
+            p.u[urow + xb + 1] = un;
+            uexp_max = max(uexp_max, expo(un));
             eo[1] = 0.f;
           }
         }
@@ -336,6 +346,10 @@ __global__ void __launch_bounds__(NT, MINB)
       make_qx(mod3(s + 1), (s + 1) & 1);
       if (t + 2 < t1) make_q(s + 2, mod3(s + 2));
     }
+  }
+  if (MODE == SWEEP_DOWNU && p.uexp) {
+    uexp_max = __reduce_max_sync(0xffffffffu, uexp_max);
+    if ((tid & 31) == 0 && uexp_max > 0) atomicMax(p.uexp, (int)uexp_max);
   }
   __syncthreads();
   if (s_fail && tid == 0) {
@@ -384,6 +398,12 @@ __global__ void __launch_bounds__(UNT, 3)
   extern __shared__ __align__(128) float smem[];
   __shared__ int s_fail;
   if (halted(p.ctl)) return;
+  // the step's refinement residual has read the exponent of u: start the
+  // maximum over the u the step's last down-pass writes (boundary values
+  // stay; they enter through bdexp)
+  if (MODE == SWEEP_UP && p.uexp && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
+      threadIdx.x == 0)
+    *p.uexp = *p.bdexp;
   float* sR = smem + UOFF_SR;
   const uint32_t bar0 = smem_addr(smem + UOFF_BAR);
   const int n = p.n, nc = p.nc, ncp1 = nc + 1;

@@ -44,6 +44,8 @@ struct Sweep3Params {
   int* fault = nullptr;            // &ctl->fault: set when a bounded wait gives up
   int* fault_info = nullptr;       // &ctl->fault_info[0]
   long long wait_polls = 1LL << 22;  // polls of a staged-plane wait before it gives up
+  int* uexp = nullptr;             // &ctl->uexp: UP resets it, DOWNU raises it
+  const int* bdexp = nullptr;      // &ctl->bdexp
 };
 
 // The refinement residual of the uniform 3-D operator A = alpha [32, 0, -2, -1]
