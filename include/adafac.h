@@ -411,6 +411,94 @@ adafac_status adafac_server_stats(adafac_server s, int* pending, int* running,
  * forgets every ticket.  Synchronises. */
 adafac_status adafac_server_destroy(adafac_server s);
 
+/* ---- Adaptive spacetrees (static trees, FP64) ---------------------------
+ *
+ * Sec. 2.1 and 2.3: level 1 exists in full (l_min = 1); a level-l cell that
+ * exists is cut into 3^dim children where refine[l-1][cell] != 0 (l = 1 ..
+ * depth-1; 3^(l*dim) bytes per level, x fastest; flags of cells that do not
+ * exist are ignored).  The leaf cells carry the d-linear element of
+ * -div(eps grad u); eps of a leaf cell coarser than the finest level is the
+ * mean of the finest cells it covers.  The unknowns are the values at the
+ * leaf nodes (the corners of the leaf cells); hanging nodes carry none, their
+ * values follow d-linearly from the coarser level.  Level l's shape
+ * functions are the pagodas of its active vertices (interior vertices whose
+ * 2^dim level-l cells all exist), a generating system over the adaptive grid:
+ * level l sees r_l = Phi_l^T (b - K u) with K the leaf stiffness, A_l =
+ * Phi_l^T K Phi_l, M_l = diag(A_l), and a cycle is Eq. 9 on that system
+ * (the options' variant, rtilde, omega, omega_tilde, omega_exp and lmin as
+ * for regular trees; the truncated R~ acts on level l's residual held on its
+ * full grid, zero at inactive positions).  The load is lumped per leaf cell:
+ * each corner of a leaf cell of width h takes h^dim / 2^dim f.  Dirichlet
+ * values are zero.
+ *   eps  host, one value (eps_is_scalar) or 3^(depth*dim) values (finest
+ *        cells, x fastest)
+ *   f    host, (3^depth + 1)^dim values at the finest-level positions, or
+ *        NULL (zero)
+ * Inputs are copied during the call.  The handle owns its device memory
+ * (allocated here), runs on `stream` (cudaStream_t; NULL = legacy default).
+ * Returns INVALID_ARG for a bad tree or options (precision MIXED, BoxMG
+ * transfers and rediscretised coarse operators are regular-tree options),
+ * OOM when an allocation fails. */
+typedef struct adafac_adaptive_s* adafac_adaptive;
+adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* refine,
+                                    const double* eps, int eps_is_scalar, const double* f,
+                                    const adafac_options* opt, void* stream,
+                                    adafac_adaptive* out);
+
+/* Enqueues n_cycles >= 0 cycles (Eq. 9 on the generating system).  Asynchronous. */
+adafac_status adafac_adaptive_cycle(adafac_adaptive h, int n_cycles);
+
+/* Eq. 10 over the vertices of the nodal space (every position that is an
+ * active vertex of some level, tested with that level's pagoda, h of that
+ * level): *abs = ||b - K u||_h, *rel = *abs / ||r_0||_h (r_0: the residual
+ * at setup or at the last adafac_adaptive_set_solution).  Either may be NULL.
+ * Synchronises. */
+adafac_status adafac_adaptive_residual_norm(adafac_adaptive h, double* rel, double* abs);
+
+/* Cycles until the normalised residual is <= rel_tol or max_cycles cycles ran;
+ * NOT_CONVERGED / DIVERGED as adafac_solve.  Synchronises every cycle. */
+adafac_status adafac_adaptive_solve(adafac_adaptive h, double rel_tol, int max_cycles,
+                                    int* cycles_done, double* rel);
+
+/* The leaf nodes: *count receives their number; idx (or NULL) their
+ * finest-level grid indices x + (3^depth + 1) (y + (3^depth + 1) z),
+ * ascending -- the order of the values of the solution calls. */
+adafac_status adafac_adaptive_nodes(adafac_adaptive h, int64_t* idx, int64_t* count);
+
+/* The iterate at the leaf nodes (host dst, count values).  Synchronises. */
+adafac_status adafac_adaptive_solution(adafac_adaptive h, double* dst);
+
+/* Sets the iterate from host src (count values, zero at boundary nodes for
+ * the zero Dirichlet data) and makes its residual the new r_0.  Synchronises. */
+adafac_status adafac_adaptive_set_solution(adafac_adaptive h, const double* src);
+
+/* Moving refinement (Sec. 5): sets dst's iterate from src, a handle on
+ * another tree of the same dim and depth.  The vertices of dst's tree take
+ * the value of src's function at their position (d-linear interpolation in
+ * the src leaf cell that holds them, so new vertices are interpolated), and
+ * the function of dst's space with those vertex values is rebuilt level by
+ * level from the coarsest (vertices hanging in dst's tree take the
+ * interpolation of their coarse cell).  dst's r_0 becomes src's, so the
+ * normalised residual keeps its reference across moves.  INVALID_ARG for
+ * trees of another shape; synchronises both streams. */
+adafac_status adafac_adaptive_transfer(adafac_adaptive dst, adafac_adaptive src);
+
+/* Level vectors of the active vertices of a level (ascending grid index of
+ * the level's (3^level + 1)^dim grid): FIELD_ACTIVE their grid indices,
+ * FIELD_R r_l of the last residual evaluation (a cycle or a norm), FIELD_BT
+ * b~_l and FIELD_G the combined correction g_l of the last cycle,
+ * FIELD_INVDIAG 1 / M_l.  *count receives the number of active vertices;
+ * dst (host, or NULL) the values.  Synchronises. */
+enum { ADAFAC_FIELD_ACTIVE = 9 };
+adafac_status adafac_adaptive_level(adafac_adaptive h, int field, int level, double* dst,
+                                    int64_t* count);
+
+/* Message of the last failing call on an adaptive handle (empty for NULL). */
+const char* adafac_adaptive_last_error(adafac_adaptive h);
+
+/* Releases the handle and its device memory.  Synchronises. */
+adafac_status adafac_adaptive_destroy(adafac_adaptive h);
+
 /* Message of the last failing call on h (or of the last failing setup when
  * h is NULL).  The pointer stays valid until the next call on h. */
 const char* adafac_last_error(adafac_handle h);

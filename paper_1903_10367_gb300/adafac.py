@@ -16,7 +16,7 @@ from . import build as _build
 
 __all__ = [
     "AdafacError", "Tree", "Options", "Tuning", "load", "default_options", "workspace_size",
-    "Solver", "FIELD", "VARIANT", "TRANSFER", "PRECISION", "RTILDE", "FORM",
+    "Solver", "AdaptiveSolver", "FIELD", "VARIANT", "TRANSFER", "PRECISION", "RTILDE", "FORM",
 ]
 
 VARIANT = {"additive": 0, "jac": 1, "pi": 2, "exp": 3}
@@ -25,7 +25,8 @@ PRECISION = {"fp64": 0, "mixed": 1}
 RTILDE = {"truncated": 0, "exact": 1}
 FORM = {"cs": 0, "fas": 1}
 PATH = {"auto": 0, "levelwise": 1, "generic": 2}
-FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8}
+FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8,
+         "active": 9}
 COARSE = {"galerkin": 0, "rediscretised": 1}
 KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,
           "fine_down": 4, "fine_up": 5, "fine_down_u": 6}
@@ -104,6 +105,18 @@ _SIGNATURES = [
     ("adafac_server_stats", _I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                  ctypes.POINTER(ctypes.c_size_t)]),
     ("adafac_server_destroy", _I, [_P]),
+    ("adafac_adaptive_setup", _I, [_I, _I, ctypes.POINTER(_P), _P, _I, _P, ctypes.POINTER(Options),
+                                   _P, ctypes.POINTER(_P)]),
+    ("adafac_adaptive_cycle", _I, [_P, _I]),
+    ("adafac_adaptive_residual_norm", _I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    ("adafac_adaptive_solve", _I, [_P, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    ("adafac_adaptive_nodes", _I, [_P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    ("adafac_adaptive_solution", _I, [_P, _P]),
+    ("adafac_adaptive_set_solution", _I, [_P, _P]),
+    ("adafac_adaptive_level", _I, [_P, _I, _I, _P, ctypes.POINTER(ctypes.c_int64)]),
+    ("adafac_adaptive_transfer", _I, [_P, _P]),
+    ("adafac_adaptive_last_error", ctypes.c_char_p, [_P]),
+    ("adafac_adaptive_destroy", _I, [_P]),
     ("adafac_last_error", ctypes.c_char_p, [_P]),
     ("adafac_destroy", _I, [_P]),
 ]
@@ -401,6 +414,116 @@ class Server:
         if self.s:
             self.lib.adafac_server_destroy(self.s)
             self.s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class AdaptiveSolver:
+    """adAFAC on a static adaptive spacetree (FP64; adafac_adaptive_*).
+
+    ``refine``: for l = 1 .. depth-1 an array of shape (3^l,)*dim (array axis
+    order, the last axis is x) whose non-zero entries cut existing level-l
+    cells; ``eps`` a scalar or one value per finest cell (shape (3^depth,)*dim);
+    ``f`` the load density at the finest-level positions (shape
+    (3^depth + 1,)*dim) or None.  The iterate lives at the leaf nodes, in the
+    order of ``nodes()`` (ascending finest-level grid index)."""
+
+    def __init__(self, dim: int, depth: int, refine, eps, f=None, opts: Options | None = None,
+                 stream=None):
+        import torch
+        self.lib = load()
+        self.dim, self.depth = dim, depth
+        n = 3 ** depth
+        self.opts = opts if opts is not None else default_options()
+        flags = [np.ascontiguousarray(np.asarray(refine[l - 1]).astype(np.uint8).reshape(-1))
+                 for l in range(1, depth)]
+        for l, a in enumerate(flags, start=1):
+            if a.size != 3 ** (l * dim):
+                raise ValueError(f"refine flags of level {l} must have {3 ** (l * dim)} entries")
+        ptrs = (ctypes.c_void_p * max(len(flags), 1))(*[a.ctypes.data for a in flags])
+        eps_a = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(-1))
+        scalar = eps_a.size == 1
+        if not scalar and eps_a.size != n ** dim:
+            raise ValueError(f"eps must be a scalar or have {n ** dim} entries")
+        f_a = None if f is None else np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+        if f_a is not None and f_a.shape != (n + 1,) * dim:
+            raise ValueError(f"f must have shape {(n + 1,) * dim}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = ctypes.c_void_p()
+        st = self.lib.adafac_adaptive_setup(dim, depth, ptrs, _host_ptr(eps_a), int(scalar),
+                                            None if f_a is None else _host_ptr(f_a),
+                                            ctypes.byref(self.opts),
+                                            ctypes.c_void_p(self.stream.cuda_stream),
+                                            ctypes.byref(self.h))
+        if st != 0:
+            raise AdafacError(st, "adafac_adaptive_setup failed")
+        count = ctypes.c_int64()
+        self._check(self.lib.adafac_adaptive_nodes(self.h, None, ctypes.byref(count)))
+        self.count = count.value
+
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.adafac_adaptive_last_error(self.h)
+            raise AdafacError(st, msg.decode() if msg else "")
+
+    def cycle(self, n: int = 1):
+        self._check(self.lib.adafac_adaptive_cycle(self.h, int(n)))
+
+    def residual_norm(self):
+        rel, ab = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.adafac_adaptive_residual_norm(self.h, ctypes.byref(rel),
+                                                           ctypes.byref(ab)))
+        return rel.value, ab.value
+
+    def solve(self, rel_tol: float = 1e-8, max_cycles: int = 2000, check: bool = True):
+        cycles, rel = ctypes.c_int(), ctypes.c_double()
+        st = self.lib.adafac_adaptive_solve(self.h, rel_tol, int(max_cycles), ctypes.byref(cycles),
+                                            ctypes.byref(rel))
+        if check:
+            self._check(st)
+        return cycles.value, rel.value
+
+    def nodes(self) -> np.ndarray:
+        out = np.empty(self.count, dtype=np.int64)
+        count = ctypes.c_int64()
+        self._check(self.lib.adafac_adaptive_nodes(self.h, _host_ptr(out), ctypes.byref(count)))
+        return out
+
+    def solution(self) -> np.ndarray:
+        out = np.empty(self.count)
+        self._check(self.lib.adafac_adaptive_solution(self.h, _host_ptr(out)))
+        return out
+
+    def set_solution(self, u):
+        a = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+        if a.size != self.count:
+            raise ValueError(f"the iterate has {self.count} leaf-node values")
+        self._check(self.lib.adafac_adaptive_set_solution(self.h, _host_ptr(a)))
+
+    def transfer_from(self, other: "AdaptiveSolver"):
+        """Takes the iterate of a solver on another tree of the same depth:
+        the old function at this tree's vertices, rebuilt in this tree's
+        space (new and hanging vertices d-linearly interpolated), with the
+        other solver's r_0 as the normalisation."""
+        self._check(self.lib.adafac_adaptive_transfer(self.h, other.h))
+
+    def level(self, name: str, level: int) -> np.ndarray:
+        count = ctypes.c_int64()
+        self._check(self.lib.adafac_adaptive_level(self.h, FIELD[name], level, None,
+                                                   ctypes.byref(count)))
+        out = np.empty(count.value)
+        self._check(self.lib.adafac_adaptive_level(self.h, FIELD[name], level, _host_ptr(out),
+                                                   ctypes.byref(count)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.adafac_adaptive_destroy(self.h)
+            self.h = ctypes.c_void_p()
 
     def __del__(self):
         try:
