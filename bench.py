@@ -417,6 +417,7 @@ def bench_ours(args, w):
         return
     cpu = None if args.no_cpu_baseline else run_oracle_sample(w, args.cpu_seconds)
     serving = run_serving(args.serve_requests) if args.serve_requests > 0 else None
+    adaptive = run_adaptive(args.adaptive_depth) if args.adaptive_depth > 0 else None
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -426,7 +427,7 @@ def bench_ours(args, w):
                    "tuning": _tuning_summary(tuning)},
            "time_to_tol_ms": ms / args.steps, "e2e": e2e, "gpu_launches": launches,
            "roofline": roofline, "clocks": clk, "cpu_baseline": cpu,
-           "fp64_comparator": fp64, "serving": serving}
+           "fp64_comparator": fp64, "serving": serving, "adaptive": adaptive}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -536,15 +537,57 @@ def run_serving(count: int, seed: int = 1903):
     srv.close()
     lat = np.array([i["latency_ms"] for i in infos_open])
     ok = ok and all(i["state"] == "done" and i["rel"] <= 1e-8 for i in infos_open)
-    single = []
-    for r in reqs:
-        t1 = time.perf_counter()
-        S = adafac.Solver(r.dim, r.depth, r.eps, r.f, o64)
-        S.solve(1e-8, 3000)
-        S.solution()
-        S.close()
-        single.append(1e3 * (time.perf_counter() - t1))
-    single = np.array(single)
+    # every request alone on one handle, one after another (setup + solve to
+    # 1e-8 + copy of u): FP64 cycles (the comparator) and mixed precision
+    def alone(opts):
+        out = []
+        for r in reqs:
+            t1 = time.perf_counter()
+            S = adafac.Solver(r.dim, r.depth, r.eps, r.f, opts)
+            S.solve(1e-8, 3000)
+            S.solution()
+            S.close()
+            out.append(1e3 * (time.perf_counter() - t1))
+        return np.array(out)
+
+    single = alone(o64)
+    single_mixed = alone(om)
+    classes = {}
+    for key in sorted({(r.dim, r.depth) for r in reqs}):
+        idx = [i for i, r in enumerate(reqs) if (r.dim, r.depth) == key]
+        m64, mmx = float(np.median(single[idx])), float(np.median(single_mixed[idx]))
+        classes[f"{key[0]}d_depth{key[1]}"] = {
+            "requests": len(idx), "fp64_alone_ms": round(m64, 3), "mixed_alone_ms": round(mmx, 3),
+            "fp64_over_mixed": round(m64 / mmx, 2)}
+    # matched load: Poisson arrivals at 0.8 x the FP64 single-instance
+    # throughput, which a one-at-a-time FP64 server sustains.  The mixed
+    # server runs live on the first requests of the stream; the FP64 server's
+    # FIFO latencies follow from its measured service times at the same
+    # arrival instants.
+    lam64 = count / (single.sum() / 1e3)
+    lam_m = 0.8 * lam64
+    n_m = min(count, 60)
+    srv = adafac.Server(pool, n_streams=32, max_running=32)
+    start = time.perf_counter()
+    tickets = []
+    for r in reqs[:n_m]:
+        target = start + r.arrival / lam_m
+        while True:
+            dt = target - time.perf_counter()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.0005))
+        tickets.append(submit(r))
+    infos_m = drain(tickets)
+    srv.close()
+    lat_m = np.array([i["latency_ms"] for i in infos_m])
+    ok = ok and all(i["state"] == "done" and i["rel"] <= 1e-8 for i in infos_m)
+    fifo, free_at = [], 0.0
+    for r, svc in zip(reqs[:n_m], single[:n_m]):
+        arr = 1e3 * r.arrival / lam_m
+        free_at = max(arr, free_at) + svc
+        fifo.append(free_at - arr)
+    fifo = np.array(fifo)
     return {
         "requests": count, "seed": seed,
         "mix": "80% 2-D depth U{3..6}, 20% 3-D depth U{3..5}; eps blocks of level-min(3, depth-1) "
@@ -564,7 +607,103 @@ def run_serving(count: int, seed: int = 1903):
             "mean_ms": float(single.mean()),
             "how": "each request alone: setup + FP64 solve to 1e-8 + copy of u, back to back"},
         "throughput_vs_fp64_single": lam_sat / (count / (single.sum() / 1e3)),
+        "mixed_single_instance": {
+            "requests_per_s": count / (single_mixed.sum() / 1e3),
+            "p50_ms": float(np.percentile(single_mixed, 50)),
+            "p99_ms": float(np.percentile(single_mixed, 99)),
+            "how": "each request alone: setup + mixed solve to 1e-8 + copy of u, back to back"},
+        "per_class_alone": classes,
+        "matched_load": {
+            "offered_requests_per_s": lam_m, "offered_load": "0.8 x FP64 single-instance throughput",
+            "requests": n_m,
+            "mixed_server": {"p50_ms": float(np.percentile(lat_m, 50)),
+                             "p99_ms": float(np.percentile(lat_m, 99))},
+            "fp64_single_instance_fifo": {
+                "p50_ms": float(np.percentile(fifo, 50)), "p99_ms": float(np.percentile(fifo, 99)),
+                "how": "FIFO queue of the measured FP64 service times at the same arrival instants"}},
     }
+
+
+def band_flags(d, L, L_base, centre, radius, width):
+    """Refinement flags of the adaptive workload's tree: depth L_base
+    everywhere and L within `width` of the circle (sphere) of `radius` about
+    `centre` (x first); a cell is cut when it reaches within width of the
+    circle, with its half-diagonal as the margin.  One flag array per level
+    l < L, shape (3^l,)*d, last axis x."""
+    ctr = np.asarray(centre, dtype=float)
+    out = []
+    for l in range(1, L):
+        n = 3 ** l
+        h = 1.0 / n
+        if l < L_base:
+            out.append(np.ones((n,) * d, dtype=bool))
+            continue
+        idx = np.indices((n,) * d)
+        c = np.stack([(idx[d - 1 - k] + 0.5) * h for k in range(d)], axis=-1)
+        r = np.sqrt(((c - ctr) ** 2).sum(-1))
+        out.append(np.abs(r - radius) <= width + 0.5 * np.sqrt(d) * h)
+    return out
+
+
+def run_adaptive(depth: int, base: int = 3, moves: int = 4, every: int = 5, shift: float = 0.01,
+                 tol: float = 1e-8):
+    """The adaptive workload on the GPU (FP64 cycles on the generating system):
+    2-D, depth `base` everywhere and `depth` within 0.05 of the circle r = 0.3
+    about the centre, f = 1, eps = 1; the band moves +x by `shift` after every
+    `every` cycles, `moves` times (the iterate carried over by the transfer),
+    then cycles to `tol`.  Reports the host build of a tree's system, the
+    transfer, the time per cycle and the cycles."""
+    import torch
+    from paper_1903_10367_gb300 import adafac
+    d = 2
+    f = np.ones((3 ** depth + 1,) * d)
+    o = adafac.default_options(precision="fp64")
+    ctr = np.array([0.5, 0.5])
+    builds, transfers, cyc_ms = [], [], []
+    t0 = time.perf_counter()
+    G = adafac.AdaptiveSolver(d, depth, band_flags(d, depth, base, ctr, 0.3, 0.05), 1.0, f, o)
+    builds.append(time.perf_counter() - t0)
+    nodes = [G.count]
+    st = torch.cuda.current_stream()
+    total = 0
+    rel = 1.0
+    for m in range(moves + 1):
+        steps = every if m < moves else 100000
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        k = 0
+        if m < moves:
+            G.cycle(steps)
+            k = steps
+        else:
+            while rel > tol and k < 5000:
+                G.cycle(8)
+                k += 8
+                rel = G.residual_norm()[0]
+        e1.record(st)
+        torch.cuda.synchronize()
+        cyc_ms.append(e0.elapsed_time(e1) / k)
+        total += k
+        if m < moves:
+            ctr = ctr + np.array([shift, 0.0])
+            t0 = time.perf_counter()
+            N = adafac.AdaptiveSolver(d, depth, band_flags(d, depth, base, ctr, 0.3, 0.05), 1.0, f, o)
+            builds.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            N.transfer_from(G)
+            transfers.append(time.perf_counter() - t0)
+            G.close()
+            G = N
+            nodes.append(G.count)
+    cycles, rel = total, G.residual_norm()[0]
+    G.close()
+    return {"dim": d, "depth": depth, "base_depth": base, "leaf_nodes": nodes,
+            "moves": moves, "every": every, "shift": shift, "cycles": cycles, "rel": rel,
+            "ms_per_cycle_median": float(np.median(cyc_ms)),
+            "build_s_median": float(np.median(builds)),
+            "transfer_ms_median": 1e3 * float(np.median(transfers)) if transfers else None,
+            "precision": "fp64", "how": "host build of the system per tree; cycles timed with "
+                                         "CUDA events (the last phase includes a norm every 8 cycles)"}
 
 
 def _traffic_from_profile(kind, w, tuning=None, table=None):
@@ -609,6 +748,8 @@ def main():
     ap.add_argument("--no-fp64-comparator", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of the autotuned ones")
+    ap.add_argument("--adaptive-depth", type=int, default=0,
+                    help="depth of the moving-band adaptive run on the GPU (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving stream run after the solve (0: skip)")
     args = ap.parse_args()
