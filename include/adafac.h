@@ -99,7 +99,22 @@ typedef struct {
                          kernels instead (a linear index decoded per vertex,
                          a warp per coarse vertex in the restriction): the
                          same steps, another summation order.  FP64 cycles
-                         always use the generic kernels.                      */
+                         always use the generic kernels.
+                         ADAFAC_PATH_BATCHED (MIXED precision, CS form, any
+                         variant but JAC with exact R~): a whole refinement
+                         step -- the FP64 residual and its norm, inner_cycles
+                         FP32 cycles of Alg. 1 and u += e -- is one launch in
+                         which a cluster of CTAs runs the steps of the cycle
+                         one after another, separated by cluster barriers.
+                         The request server runs the steps of all its running
+                         BATCHED requests of one dimension and cluster size
+                         in one launch, a cluster per request; every vertex
+                         is computed the same way whatever the batch or the
+                         cluster size, so a request's iterates do not depend
+                         on the requests it runs with.  AUTO takes this path
+                         too for MIXED solves it covers whose finest grid has
+                         at most 1024 vertices (2-D depth <= 3, 3-D depth <=
+                         2) and that the fused 3-D kernels do not take.       */
   int coarse_op;      /* ADAFAC_COARSE_GALERKIN (default): A_{l-1} =
                          P_l^T A_l P_l (Sec. 2.2); ADAFAC_COARSE_REDISCRETISED:
                          the d-linear FEM operator of level l-1 with the eps of
@@ -109,7 +124,8 @@ typedef struct {
                          correction levels one by one below the finest)      */
 } adafac_options;
 
-enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1, ADAFAC_PATH_GENERIC = 2 };
+enum { ADAFAC_PATH_AUTO = 0, ADAFAC_PATH_LEVELWISE = 1, ADAFAC_PATH_GENERIC = 2,
+       ADAFAC_PATH_BATCHED = 3 };
 enum { ADAFAC_COARSE_GALERKIN = 0, ADAFAC_COARSE_REDISCRETISED = 1 };
 
 /* Fills *opt with the defaults: JAC, d-linear, FP64, truncated R~, CS,
@@ -208,6 +224,20 @@ adafac_status adafac_reset(adafac_handle h);
  * polls < 0.  Synchronises (cycles already enqueued keep the old limit). */
 adafac_status adafac_set_wait_limit(adafac_handle h, long long polls);
 
+/* CTAs per instance of the batched path (ADAFAC_PATH_BATCHED).  Performance
+ * extension with no counterpart in the paper: the cluster of CTAs that runs
+ * a handle's refinement steps.  Setup picks one CTA when the FP32 vectors fit
+ * into 100 KB of shared memory (they are then held there), else a power of
+ * two from the size of the finest grid (about 8 vertices per thread, at most
+ * 16, or 8 where the device cannot place clusters of 16); every choice
+ * computes the same iterates bit for bit.  adafac_set_batch_cluster takes a
+ * power of two in 1 .. that limit (INVALID_ARG otherwise, or when the handle
+ * does not run the batched path); adafac_batch_cluster writes the current
+ * value to *ctas.
+ * Neither call touches the device. */
+adafac_status adafac_set_batch_cluster(adafac_handle h, int ctas);
+adafac_status adafac_batch_cluster(adafac_handle h, int* ctas);
+
 /* Inspection of internal per-level arrays (for tests and diagnostics).
  * field: ADAFAC_FIELD_*; level: 1..L.  Copies the array as doubles to dst
  * (host or device) and writes its length to *count (pass dst = NULL to query
@@ -265,7 +295,8 @@ enum {
   ADAFAC_KERNEL_FINE_DOWN_U = 6,   /* 3-D uniform path: last down-pass of a
                                       refinement step, which also adds the
                                       correction to the FP64 iterate       */
-  ADAFAC_KERNEL_KINDS = 7
+  ADAFAC_KERNEL_BATCH_STEP = 7,    /* path BATCHED: a whole refinement step */
+  ADAFAC_KERNEL_KINDS = 8
 };
 adafac_status adafac_timing(adafac_handle h, int enable);
 adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,

@@ -24,12 +24,12 @@ TRANSFER = {"dlinear": 0, "boxmg": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 RTILDE = {"truncated": 0, "exact": 1}
 FORM = {"cs": 0, "fas": 1}
-PATH = {"auto": 0, "levelwise": 1, "generic": 2}
+PATH = {"auto": 0, "levelwise": 1, "generic": 2, "batched": 3}
 FIELD = {"u": 0, "b": 1, "r": 2, "bt": 3, "g": 4, "t": 5, "P": 6, "stencil": 7, "invdiag": 8,
          "active": 9}
 COARSE = {"galerkin": 0, "rediscretised": 1}
 KERNEL = {"fine_residual": 0, "fine_update": 1, "fine_restrict": 2, "refine": 3,
-          "fine_down": 4, "fine_up": 5, "fine_down_u": 6}
+          "fine_down": 4, "fine_up": 5, "fine_down_u": 6, "batch_step": 7}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "DIVERGED", 4: "TIMEOUT", 5: "CUDA",
           6: "NOT_CONVERGED"}
 
@@ -90,6 +90,8 @@ _SIGNATURES = [
     ("adafac_set_boundary", _I, [_P, _P, _I]),
     ("adafac_reset", _I, [_P]),
     ("adafac_set_wait_limit", _I, [_P, ctypes.c_longlong]),
+    ("adafac_set_batch_cluster", _I, [_P, _I]),
+    ("adafac_batch_cluster", _I, [_P, ctypes.POINTER(_I)]),
     ("adafac_get_field", _I, [_P, _I, _I, _P, _I, ctypes.POINTER(ctypes.c_size_t)]),
     ("adafac_history", _I, [_P, _P, _I, ctypes.POINTER(_I)]),
     ("adafac_launch_count", _I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -281,6 +283,15 @@ class Solver:
         """Poll limit of the sweeps' bounded waits (0: every wait gives up at
         once, which exercises the timeout path)."""
         _check(self.lib.adafac_set_wait_limit(self.h, int(polls)), self.h)
+
+    def set_batch_cluster(self, ctas: int):
+        """CTAs per instance of the batched path (a power of two)."""
+        _check(self.lib.adafac_set_batch_cluster(self.h, int(ctas)), self.h)
+
+    def batch_cluster(self) -> int:
+        c = _I(0)
+        _check(self.lib.adafac_batch_cluster(self.h, ctypes.byref(c)), self.h)
+        return c.value
 
     def set_solution(self, u):
         if isinstance(u, np.ndarray):

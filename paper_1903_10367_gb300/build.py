@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libadafac.so")
 SOURCES = ["setup.cu", "cycle.cu", "level.cu", "sweep3.cu", "coarse3.cu", "api.cu", "noalloc.cu",
-           "server.cu", "adaptive.cu"]
+           "server.cu", "adaptive.cu", "batch.cu"]
 HEADERS = ["engine.h", "common.cuh", "sweep3.cuh", "mbarrier.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -107,6 +107,13 @@ struct adafac_handle_s {
   Refine3Params rf;
   // launch shapes of the fine residual and update of the level path (autotuned)
   GridShape res_shape, upd_shape;
+  // batched refinement steps (path BATCHED): the instance on the device, its
+  // host image, the CTAs per instance
+  bool batched = false;
+  BatchItem* bitem = nullptr;
+  BatchItem bitem_host;
+  int bC = 1;
+  int bonchip = 0;           // bytes of FP32 vectors kept on chip at one CTA (0: none)
   // CUDA graphs of whole cycle batches / refinement steps
   bool use_graphs = true;
   cudaStream_t cap = nullptr;
@@ -160,7 +167,11 @@ bool valid_options(const adafac_options* o, std::string* why) {
   if (o->form == ADAFAC_FORM_FAS && o->precision != ADAFAC_PRECISION_FP64)
     return *why = "FAS form requires FP64 precision", false;
   if (o->inner_cycles < 1) return *why = "inner_cycles must be >= 1", false;
-  if (o->path < 0 || o->path > 2) return *why = "path out of range", false;
+  if (o->path < 0 || o->path > 3) return *why = "path out of range", false;
+  if (o->path == ADAFAC_PATH_BATCHED &&
+      (o->precision != ADAFAC_PRECISION_MIXED ||
+       (o->variant == ADAFAC_VARIANT_JAC && o->rtilde == ADAFAC_RTILDE_EXACT)))
+    return *why = "path BATCHED needs MIXED precision and the truncated R~ for JAC", false;
   if (o->coarse_op < 0 || o->coarse_op > 1) return *why = "coarse_op out of range", false;
   if (o->lmin < 1) return *why = "lmin must be >= 1", false;
   if (!(o->omega > 0.0) || !(o->omega_tilde >= 0.0) || !(o->omega_exp > 0.0))
@@ -187,6 +198,22 @@ bool fast3_eligible(const adafac_handle_s* h) {
          o.form == ADAFAC_FORM_CS && o.rtilde == ADAFAC_RTILDE_TRUNCATED &&
          (o.variant == ADAFAC_VARIANT_JAC || o.variant == ADAFAC_VARIANT_ADDITIVE ||
           o.variant == ADAFAC_VARIANT_EXP);
+}
+
+// Path BATCHED, or AUTO on the smallest grids (at most kAutoBatchMaxV fine
+// vertices: 2-D depth <= 3, 3-D depth <= 2) outside the fused 3-D path: there
+// a refinement step in one launch on one CTA, with its vectors in shared
+// memory, is faster than a graph of level kernels, and the request server
+// batches such requests into shared launches.
+constexpr long long kAutoBatchMaxV = 1024;
+
+bool batched_choice(const adafac_handle_s* h) {
+  const adafac_options& o = h->opt;
+  if (o.path == ADAFAC_PATH_BATCHED) return true;
+  const bool covered = o.precision == ADAFAC_PRECISION_MIXED && o.form == ADAFAC_FORM_CS &&
+                       !(o.variant == ADAFAC_VARIANT_JAC && o.rtilde == ADAFAC_RTILDE_EXACT);
+  return o.path == ADAFAC_PATH_AUTO && covered && !h->fast3 &&
+         ipow_ll(ipow_ll(3, h->L) + 1, h->D) <= kAutoBatchMaxV;
 }
 
 // Carves every array of the handle (measure-only when base is null).
@@ -243,6 +270,7 @@ void carve(adafac_handle h, Carver& cv) {
   h->ub = cv.take<double>(Vf);
   h->b = cv.take<double>(Vf);
   if (h->fast3) h->bq = cv.take<double>(Vf);
+  if (h->batched) h->bitem = cv.take<BatchItem>(1);
   if (!h->eps_scalar) {
     h->eps = cv.take<double>(ipow_ll(h->lev[L].n, D));
     if (mixed) h->eps32 = cv.take<float>(ipow_ll(h->lev[L].n, D));
@@ -267,6 +295,7 @@ void carve(adafac_handle h, Carver& cv) {
   if (mixed)
     h->npartials = std::max(h->npartials, D == 2 ? residual_g_blocks<2>(h->lev[L].n)
                                                  : residual_g_blocks<3>(h->lev[L].n));
+  if (h->batched) h->npartials = std::max<long long>(h->npartials, batch_units(Vf));
   h->partials = cv.take<double>(h->npartials);
   h->ctl = cv.take<Control>(1);
   h->hist = cv.take<double>(kHistCap);
@@ -532,6 +561,51 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
       cudaGetLastError();
       h->fast3 = false;  // no tensor-map encoder: level-by-level kernels
     }
+  }
+  if (h->batched) {
+    BatchItem& it = h->bitem_host;
+    it = BatchItem();
+    it.L = L;
+    it.lmin = h->opt.lmin;
+    it.variant = h->opt.variant;
+    it.nunits = (int)batch_units(fine.V);
+    it.omega = h->cp32.omega;
+    it.omega_t = h->cp32.omega_tilde;
+    it.hfac = fine.v64.hfac;
+    it.hfac32 = (float)fine.v64.hfac;
+    it.eps0 = h->eps0;
+    it.eps0f = (float)h->eps0;
+    it.hD = std::pow(1.0 / fine.n, D);
+    it.eps = h->eps_scalar ? nullptr : h->eps;
+    it.eps32 = h->eps_scalar ? nullptr : h->eps32;
+    it.u = h->u;
+    it.b = h->b;
+    it.e = h->e32;
+    it.rhs = h->rhs32;
+    it.partials = h->partials;
+    it.ctl = h->ctl;
+    it.hist = h->hist;
+    it.hist_cap = kHistCap;
+    for (int k = 0; k < 125; ++k) it.stilde[k] = h->cp32.stilde[k];
+    for (int l = 1; l <= L; ++l) {
+      const LevelData& lv = h->lev[l];
+      BatchLevel& bl = it.lev[l];
+      bl.n = lv.n;
+      bl.V = lv.V;
+      bl.invd = lv.invd32;
+      bl.invd0 = lv.v32.invd0;
+      bl.P = lv.P32;
+      bl.r = lv.r32;
+      bl.bt = lv.bt32;
+      bl.g = lv.g32;
+      bl.t = lv.t32;
+      bl.gscale =
+          h->opt.variant == ADAFAC_VARIANT_EXP ? (float)std::pow(h->opt.omega_exp, (double)(L - l)) : 1.0f;
+    }
+    h->bonchip = batch_onchip_bytes(it);
+    h->bC = batch_cluster_size(fine.V, h->bonchip);
+    if (cudaMemcpyAsync(h->bitem, &it, sizeof(BatchItem), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return check_cuda(h, "copy batch item");
   }
   cudaMemsetAsync(h->u, 0, sizeof(double) * fine.V, s);
   Control c{};
@@ -838,8 +912,31 @@ void run_graph(adafac_handle h, long key, F&& enqueue) {
   h->launches += it->second.kernels;
 }
 
+// One refinement step of the batched path with k FP32 cycles (k = 0: only
+// the FP64 residual and its norm), this handle alone in the launch.
+void batch_step(adafac_handle h, int k) {
+  BatchLaunch bl;
+  bl.item[0] = h->bitem;
+  bl.k[0] = k;
+  bl.count = 1;
+  bl.dyn_bytes = h->bC == 1 ? h->bonchip : 0;
+  timed(h, ADAFAC_KERNEL_BATCH_STEP, [&] {
+    const cudaError_t e = launch_batch_step(h->D, h->bC, bl, h->stream);
+    if (e != cudaSuccess) h->err = std::string("batched step: ") + cudaGetErrorString(e);
+  });
+  h->launches += 1;
+}
+
 template <int D>
 void enqueue_cycles(adafac_handle h, int n) {
+  if (h->batched) {
+    while (n > 0) {
+      const int k = n < h->opt.inner_cycles ? n : h->opt.inner_cycles;
+      batch_step(h, k);
+      n -= k;
+    }
+    return;
+  }
   if (h->opt.precision == ADAFAC_PRECISION_FP64) {
     while (n > 0) {
       const int b = n < 8 ? n : 8;
@@ -939,6 +1036,14 @@ void smoothed_restriction_stencil(int D, double* out) { smoothed_stencil(D, out)
 // Internal accessors for the request server (same library, not part of the
 // C ABI).
 Control* handle_control(adafac_handle h) { return h->ctl; }
+
+const BatchItem* handle_batch_item(adafac_handle h, int* D, int* C, int* onchip_bytes) {
+  if (!h || !h->batched) return nullptr;
+  if (D) *D = h->D;
+  if (C) *C = h->bC;
+  if (onchip_bytes) *onchip_bytes = h->bonchip;
+  return h->bitem;
+}
 
 adafac_status handle_arm(adafac_handle h, double rel_tol) {
   adafac_status st = write_ctl_field(h, offsetof(Control, tol), rel_tol);
@@ -1138,6 +1243,7 @@ adafac_status adafac_workspace_size(const adafac_tree* tree, const adafac_option
     tmp.eps_scalar = scalar;
     tmp.uniform = scalar && opt->transfer == ADAFAC_TRANSFER_DLINEAR;
     tmp.fast3 = fast3_eligible(&tmp);
+    tmp.batched = batched_choice(&tmp);
     Carver cv;
     carve(&tmp, cv);
     // lay the arrays out once more against a fake, never dereferenced base:
@@ -1195,6 +1301,7 @@ adafac_status adafac_setup(const adafac_tree* tree, const double* eps, int eps_i
   }
   h->uniform = h->eps_scalar && opt->transfer == ADAFAC_TRANSFER_DLINEAR;
   h->fast3 = fast3_eligible(h);
+  h->batched = batched_choice(h);
   Carver measure;
   carve(h, measure);
   const size_t need = measure.off + 256;
@@ -1283,7 +1390,9 @@ adafac_status adafac_solve(adafac_handle h, double rel_tol, int max_cycles, int*
   }
   if (!done && !diverged) {
     // residual of the final iterate, recorded like a cycle evaluation
-    if (mixed) {
+    if (h->batched) {
+      batch_step(h, 0);
+    } else if (mixed) {
       if (h->D == 2) refine_residual<2>(h);
       else refine_residual<3>(h);
     } else {
@@ -1477,6 +1586,23 @@ adafac_status adafac_set_wait_limit(adafac_handle h, long long polls) {
   return ADAFAC_OK;
 }
 
+adafac_status adafac_set_batch_cluster(adafac_handle h, int ctas) {
+  if (!h) return fail(nullptr, ADAFAC_ERR_INVALID_ARG, "null handle");
+  if (!h->batched) return fail(h, ADAFAC_ERR_INVALID_ARG, "handle does not run the batched path");
+  if (ctas < 1 || (ctas & (ctas - 1)) || ctas > batch_max_cluster())
+    return fail(h, ADAFAC_ERR_INVALID_ARG,
+                "ctas must be a power of two in 1.." + std::to_string(batch_max_cluster()));
+  h->bC = ctas;
+  return ADAFAC_OK;
+}
+
+adafac_status adafac_batch_cluster(adafac_handle h, int* ctas) {
+  if (!h || !ctas) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
+  if (!h->batched) return fail(h, ADAFAC_ERR_INVALID_ARG, "handle does not run the batched path");
+  *ctas = h->bC;
+  return ADAFAC_OK;
+}
+
 adafac_status adafac_launch_count(adafac_handle h, uint64_t* count) {
   if (!h || !count) return fail(h, ADAFAC_ERR_INVALID_ARG, "null argument");
   *count = h->launches;
@@ -1520,7 +1646,7 @@ adafac_status adafac_autotune(adafac_handle h, int repeats, adafac_tuning* out) 
   if (repeats < 1 || repeats > 1000) return fail(h, ADAFAC_ERR_INVALID_ARG, "repeats must be in 1..1000");
   *out = adafac_tuning();
   const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
-  const bool level = mixed && !h->fast3 && h->opt.path != ADAFAC_PATH_GENERIC;
+  const bool level = mixed && !h->fast3 && !h->batched && h->opt.path != ADAFAC_PATH_GENERIC;
   if (!h->fast3 && !level) return ADAFAC_OK;  // nothing tunable: path 0
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda(h, "autotune device");

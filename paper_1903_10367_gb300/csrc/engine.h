@@ -70,7 +70,79 @@ struct Control {
   int bdexp;          // largest biased binary exponent of the Dirichlet values of u
 };
 
+// ---- batched refinement steps (batch.cu) -------------------------------------
+// One instance of the batched path: everything a refinement step of a mixed
+// solve touches, on the device (the handle's workspace holds it).  Level l =
+// 1 .. L; P of level l weights level l's vertices towards the corners of
+// their level-(l-1) cell (BoxMG), null for d-linear weights.
+struct BatchLevel {
+  int n = 0;                   // cells per axis
+  int pad = 0;
+  long long V = 0;             // vertices (n + 1)^D
+  const float* invd = nullptr; // 1/diag per vertex, or null -> invd0
+  const float* P = nullptr;
+  float* r = nullptr;          // r_l (level L: the FP32 residual)
+  float* bt = nullptr;         // b~_l
+  float* g = nullptr;          // g_l = c_l - c~_l
+  float* t = nullptr;          // t_l = g_l + P q_{l-1}
+  float invd0 = 0.f;
+  float gscale = 1.f;          // EXP: omega_exp^(L - l)
+};
+
+struct BatchItem {
+  int L = 0, lmin = 1, variant = V_JAC, nunits = 0;
+  float omega = 0.6f, omega_t = 0.6f;
+  float hfac32 = 1.f, eps0f = 0.f;   // FP32 fine operator: h^(D-2), scalar eps
+  double hfac = 1.0, eps0 = 0.0;     // FP64 fine operator
+  double hD = 0.0;                   // h^D of the finest level (Eq. 10)
+  const double* eps = nullptr;       // per-cell eps (null: scalar eps0)
+  const float* eps32 = nullptr;
+  double* u = nullptr;
+  const double* b = nullptr;
+  float* e = nullptr;                // correction of the FP32 cycles
+  float* rhs = nullptr;              // FP32 right-hand side (the FP64 residual)
+  double* partials = nullptr;        // one norm partial per unit of vertices
+  Control* ctl = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int pad = 0;
+  float stilde[125] = {};            // truncated smoothed restriction (5^D)
+  BatchLevel lev[kMaxLevels + 1];
+};
+
+constexpr int kBatchThreads = 512;   // threads per CTA; a unit is this many vertices
+constexpr int kBatchMax = 64;        // instances per launch
+
+struct BatchLaunch {
+  const BatchItem* item[kBatchMax];
+  int k[kBatchMax];                  // FP32 cycles of the step, per instance
+  Control* mirror = nullptr;         // optional: mirror[i] = control block of item i at the end
+  int count = 0;
+  int dyn_bytes = 0;                 // one-CTA instances: shared memory for their vectors
+};
+
+// Shared memory a one-CTA instance may take for its FP32 vectors.
+constexpr int kBatchOnchipBytes = 100 << 10;
+// Bytes of the FP32 vectors an instance keeps on chip when it runs on one
+// CTA, or 0 when they exceed kBatchOnchipBytes.
+int batch_onchip_bytes(const BatchItem& host_item);
+
+// CTAs per instance (a power of two, at most 16) for a fine grid of V
+// vertices: one when the vectors fit on chip (onchip_bytes > 0).
+int batch_cluster_size(long long V, int onchip_bytes);
+// The largest cluster the device places (16, else 8).
+int batch_max_cluster();
+// Norm partials the batched step writes for a fine grid of V vertices.
+inline long long batch_units(long long V) { return (V + kBatchThreads - 1) / kBatchThreads; }
+// One launch: a cluster of C CTAs per item, every item of dimension D and
+// cluster size C.  Returns the launch's error.
+cudaError_t launch_batch_step(int D, int C, const BatchLaunch& bl, cudaStream_t s);
+
 // ---- handle internals used by the request server ---------------------------
+// The batched path's instance of a handle (null unless the handle runs the
+// batched path), its dimension, cluster size and on-chip bytes
+// (batch_onchip_bytes).
+const BatchItem* handle_batch_item(adafac_handle h, int* D, int* C, int* onchip_bytes);
 Control* handle_control(adafac_handle h);
 // ctl->tol = rel_tol, ctl->done = 0 (synchronises the handle's stream)
 adafac_status handle_arm(adafac_handle h, double rel_tol);

@@ -21,6 +21,12 @@
 // kSmallBytes of workspace) run on high-priority streams so that their short
 // kernels are scheduled ahead of the blocks of large ones.  A request submitted
 // while others run is admitted as soon as a slot and memory are free.
+// Requests set up with path BATCHED do not get launches of their own: the
+// launcher groups them by dimension and cluster size, and one launch of the
+// batched kernel advances every request of a group by one refinement step (a
+// cluster of CTAs per request), followed by one copy of all their control
+// blocks.  A group has one launch in flight at a time; requests that became
+// ready meanwhile join its next launch.
 // Latency is measured on the host from submission to the moment the solution
 // is in host memory.
 #include <algorithm>
@@ -116,11 +122,27 @@ struct Request {
   int slot = -1;
   bool inflight = false;
   int enqueued = 0;
+  // batched path: the instance on the device and its launch group
+  const BatchItem* bitem = nullptr;
+  int group = -1;
+  int onchip = 0;               // shared-memory bytes of its vectors at one CTA
+  int step_k = 0;               // cycles of the launch in flight
   // result
   int cycles = 0;
   double rel = 0.0;
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
   std::vector<double> u;
+};
+
+// One launch group of batched requests (same dimension and cluster size).
+struct BatchGroup {
+  int D = 0, C = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  Control* d_mirror = nullptr;   // device: control blocks written by the launch
+  Control* h_mirror = nullptr;   // pinned copy of them
+  std::vector<Request*> members; // requests of the launch in flight
+  bool inflight = false;
 };
 
 }  // namespace
@@ -147,6 +169,8 @@ struct adafac_server_s {
   int device = 0;
   Control* ctl_slots = nullptr;  // pinned, one per running request
   std::vector<int> free_slots;
+  std::map<int, BatchGroup> groups;  // batched launch groups by D * 64 + C (launcher)
+  int batch_priority = 0;
 };
 
 namespace {
@@ -215,6 +239,9 @@ void admit(adafac_server_s* S, Request* r) {
   }
   r->inflight = false;
   r->enqueued = 0;
+  int D = 0, C = 0;
+  r->bitem = handle_batch_item(r->h, &D, &C, &r->onchip);
+  r->group = r->bitem ? D * 64 + C : -1;
   std::lock_guard<std::mutex> g(S->mu);
   S->running.push_back(r->ticket);
   S->in_setup -= 1;
@@ -271,11 +298,81 @@ void complete(adafac_server_s* S, Request* r) {
   finish(S, r, st == ADAFAC_OK ? ADAFAC_REQUEST_DONE : ADAFAC_REQUEST_FAILED, st, why);
 }
 
+// The launch group of a batched request (created on first use; launcher
+// thread only).  Null when its stream or buffers cannot be made.
+BatchGroup* group_of(adafac_server_s* S, const Request* r) {
+  auto it = S->groups.find(r->group);
+  if (it != S->groups.end()) return it->second.stream ? &it->second : nullptr;
+  BatchGroup& G = S->groups[r->group];
+  G.D = r->group / 64;
+  G.C = r->group % 64;
+  if (cudaStreamCreateWithPriority(&G.stream, cudaStreamNonBlocking, S->batch_priority) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&G.d_mirror, sizeof(Control) * kBatchMax) != cudaSuccess ||
+      cudaMallocHost(&G.h_mirror, sizeof(Control) * kBatchMax) != cudaSuccess) {
+    cudaGetLastError();
+    if (G.stream) cudaStreamDestroy(G.stream);
+    G.stream = nullptr;
+    return nullptr;
+  }
+  return &G;
+}
+
+// hands an ended request to the service threads (launcher thread)
+void hand_over(adafac_server_s* S, Request* r) {
+  std::lock_guard<std::mutex> g(S->mu);
+  S->running.erase(std::find(S->running.begin(), S->running.end(), r->ticket));
+  S->completing.push_back(r);
+  S->cv.notify_all();
+}
+
+// One launch of the batched kernel for the ready requests of a group, then
+// one copy of their control blocks.  Returns false if nothing was launched.
+bool launch_group(adafac_server_s* S, BatchGroup& G, std::vector<Request*>& ready) {
+  BatchLaunch bl;
+  G.members.clear();
+  for (Request* r : ready) {
+    if ((int)G.members.size() == kBatchMax) break;
+    int k = std::min(r->opt.inner_cycles, r->max_cycles - r->enqueued);
+    if (k < 1) continue;
+    bl.item[bl.count] = r->bitem;
+    bl.k[bl.count] = k;
+    bl.count += 1;
+    if (G.C == 1) bl.dyn_bytes = std::max(bl.dyn_bytes, r->onchip);
+    r->step_k = k;
+    G.members.push_back(r);
+  }
+  if (!bl.count) return false;
+  bl.mirror = G.d_mirror;
+  cudaError_t e = launch_batch_step(G.D, G.C, bl, G.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G.h_mirror, G.d_mirror, sizeof(Control) * bl.count,
+                        cudaMemcpyDeviceToHost, G.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(G.ev, G.stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (Request* r : G.members) {
+      r->host_ctl->fault = 1;  // reported as a failed request
+      hand_over(S, r);
+    }
+    G.members.clear();
+    return true;
+  }
+  for (Request* r : G.members) {
+    r->inflight = true;
+    r->enqueued += r->step_k;
+  }
+  G.inflight = true;
+  return true;
+}
+
 // Launcher: keeps a batch in flight for every running request and hands
 // ended requests to the service thread.  It never waits on the device.
 void launcher_loop(adafac_server_s* S) {
   cudaSetDevice(S->device);
   std::vector<Request*> run;
+  std::map<int, std::vector<Request*>> ready;
   while (!S->stop.load()) {
     bool busy = false;
     run.clear();
@@ -283,7 +380,34 @@ void launcher_loop(adafac_server_s* S) {
       std::lock_guard<std::mutex> g(S->mu);
       for (int64_t t : S->running) run.push_back(S->all[t]);
     }
+    // batched groups whose launch ended: their control blocks are in host memory
+    for (auto& kv : S->groups) {
+      BatchGroup& G = kv.second;
+      if (!G.inflight) continue;
+      const cudaError_t q = cudaEventQuery(G.ev);
+      if (q == cudaErrorNotReady) continue;
+      busy = true;
+      G.inflight = false;
+      if (q != cudaSuccess) cudaGetLastError();
+      for (size_t i = 0; i < G.members.size(); ++i) {
+        Request* r = G.members[i];
+        r->inflight = false;
+        if (q != cudaSuccess) r->host_ctl->fault = 1;
+        else *r->host_ctl = G.h_mirror[i];
+      }
+    }
+    ready.clear();
     for (Request* r : run) {
+      if (r->bitem) {
+        if (r->inflight) continue;
+        if (r->enqueued > 0 && ended(r)) {
+          busy = true;
+          hand_over(S, r);
+        } else {
+          ready[r->group].push_back(r);
+        }
+        continue;
+      }
       if (!r->inflight) {
         launch_batch(r);
         busy = true;
@@ -300,10 +424,20 @@ void launcher_loop(adafac_server_s* S) {
         launch_batch(r);
         continue;
       }
-      std::lock_guard<std::mutex> g(S->mu);
-      S->running.erase(std::find(S->running.begin(), S->running.end(), r->ticket));
-      S->completing.push_back(r);
-      S->cv.notify_all();
+      hand_over(S, r);
+    }
+    for (auto& kv : ready) {
+      BatchGroup* G = group_of(S, kv.second.front());
+      if (!G) {
+        for (Request* r : kv.second) {
+          r->host_ctl->fault = 1;
+          hand_over(S, r);
+        }
+        busy = true;
+        continue;
+      }
+      if (G->inflight) continue;
+      if (launch_group(S, *G, kv.second)) busy = true;
     }
     if (!busy) {
       std::unique_lock<std::mutex> lk(S->mu);
@@ -356,6 +490,8 @@ void service_loop(adafac_server_s* S) {
 
 // after both threads stopped: release whatever is still on the device
 void drain_all(adafac_server_s* S) {
+  for (auto& kv : S->groups)
+    if (kv.second.stream) cudaStreamSynchronize(kv.second.stream);
   std::vector<Request*> left;
   {
     std::lock_guard<std::mutex> g(S->mu);
@@ -411,6 +547,7 @@ adafac_status adafac_server_create(size_t device_bytes, int n_streams, int max_r
     cudaGetLastError();
     least = greatest = 0;
   }
+  S->batch_priority = greatest;
   for (int i = 0; i < n_streams; ++i) {
     cudaStream_t a = nullptr, b = nullptr;
     if (cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, least) != cudaSuccess ||
@@ -526,6 +663,13 @@ adafac_status adafac_server_destroy(adafac_server S) {
   for (auto& kv : S->all) delete kv.second;
   for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
   for (cudaStream_t s : S->fast_streams) cudaStreamDestroy(s);
+  for (auto& kv : S->groups) {
+    BatchGroup& G = kv.second;
+    if (G.stream) cudaStreamDestroy(G.stream);
+    if (G.ev) cudaEventDestroy(G.ev);
+    if (G.d_mirror) cudaFree(G.d_mirror);
+    if (G.h_mirror) cudaFreeHost(G.h_mirror);
+  }
   cudaFreeHost(S->ctl_slots);
   cudaFree(S->pool_base);
   delete S->pool;
