@@ -413,7 +413,13 @@ typedef struct {
 
 /* Allocates the pool (one cudaMalloc) and starts the worker.  OOM if the
  * pool cannot be allocated; INVALID_ARG for n_streams outside 1..256 or
- * max_running < 1. */
+ * max_running < 1.  Requests run on up to 2 n_streams streams plus one per
+ * batched launch group: start the process with CUDA_DEVICE_MAX_CONNECTIONS
+ * set to 32 (read when the CUDA context is created; the driver's default is
+ * 8), so that streams do not share hardware work queues and a small
+ * request's kernels do not wait behind a large one's (measured on the
+ * serving mix at 0.8 x saturated load: p50 latency 86 ms with 8 queues, 31
+ * ms with 32). */
 adafac_status adafac_server_create(size_t device_bytes, int n_streams, int max_running,
                                    adafac_server* out);
 

@@ -372,7 +372,10 @@ class Solver:
 class Server:
     """Continuous-batching request server (adafac_server_*): solves submitted
     from the host are admitted by device-memory footprint, run concurrently on
-    the server's streams and return their solutions to host memory."""
+    the server's streams and return their solutions to host memory.  Requests
+    on the batched path share launches.  Start the process with
+    CUDA_DEVICE_MAX_CONNECTIONS=32 (before anything creates the CUDA
+    context) so that the streams get hardware work queues of their own."""
 
     def __init__(self, device_bytes: int, n_streams: int = 16, max_running: int = 64):
         self.lib = load()
