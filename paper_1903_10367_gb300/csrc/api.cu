@@ -768,12 +768,19 @@ void refine_residual(adafac_handle h) {
   h->launches += 2;
 }
 
+// k FP32 cycles on the correction equation and u += e (the refinement step
+// without its leading residual)
 template <int D>
-void mixed_step(adafac_handle h, int k) {
-  refine_residual<D>(h);
+void mixed_body(adafac_handle h, int k) {
   for (int i = 0; i < k; ++i) fp32_cycle<D>(h);
   launch_refine_update(h->u, h->e32, h->lev[h->L].V, h->ctl, h->stream);
   h->launches += 1;
+}
+
+template <int D>
+void mixed_step(adafac_handle h, int k) {
+  refine_residual<D>(h);
+  mixed_body<D>(h, k);
 }
 
 // Coarse levels L-1 .. 1 of an FP32 cycle whose level L-1 vectors came from a
@@ -828,17 +835,28 @@ void coarse_chain32(adafac_handle h) {
 //   buffer), UPE (up-pass of cycle j from that e), coarse levels;
 //   DOWNU: down-pass of cycle k and u += e.  Returns the zero buffer of the
 //   next step.
+void fast3_refine(adafac_handle h) {
+  const Refine3Params rf = h->rf;
+  // the scale of the fixed-point residual follows the largest |u|: ctl->uexp
+  // is exact here (set by the last down-pass before it, or by the call that
+  // set u)
+  timed(h, ADAFAC_KERNEL_REFINE, [&] { launch_refine3(rf, h->stream); });
+  launch_norm_finalize(h->partials, refine3_blocks(h->lev[h->L].n, rf.zc), h->ctl, h->hist,
+                       kHistCap, 0, h->stream);
+  h->launches += 2;
+}
+
+// The cycles of a refinement step of the 3-D uniform path after its residual.
+int fast3_body(adafac_handle h, int k, int ebase);
+
 int fast3_step(adafac_handle h, int k, int ebase) {
+  fast3_refine(h);
+  return fast3_body(h, k, ebase);
+}
+
+int fast3_body(adafac_handle h, int k, int ebase) {
   const int L = h->L;
   cudaStream_t s = h->stream;
-  Refine3Params rf = h->rf;
-  // the scale of the fixed-point residual follows the largest |u|: ctl->uexp
-  // is exact here (set by the previous step's last down-pass, or by the call
-  // that set u)
-  timed(h, ADAFAC_KERNEL_REFINE, [&] { launch_refine3(rf, s); });
-  launch_norm_finalize(h->partials, refine3_blocks(h->lev[L].n, rf.zc), h->ctl, h->hist,
-                       kHistCap, 0, s);
-  h->launches += 2;
   Sweep3Params p = h->sw;
   const int lmin = h->opt.lmin;
   p.q = L - 1 == lmin ? h->lev[lmin].g32 : h->lev[L - 1].t32;
@@ -959,6 +977,35 @@ void enqueue_cycles(adafac_handle h, int n) {
       run_graph(h, 2000 + k, [&] { mixed_step<D>(h, k); });
     }
     n -= k;
+  }
+}
+
+// The refinement residual of u and its norm alone: the start of a mixed
+// solve on the fused or level kernels.
+template <int D>
+void enqueue_refine_only(adafac_handle h) {
+  if (h->fast3) run_graph(h, 6000, [&] { fast3_refine(h); });
+  else run_graph(h, 6001, [&] { refine_residual<D>(h); });
+}
+
+// k FP32 cycles, u += e, then the residual of the new u and its norm: the
+// steps of a mixed solve after its first residual.  The norm that ends the
+// solve is the last work enqueued, so no step runs (or returns at entry)
+// after it.
+template <int D>
+void enqueue_solve_group(adafac_handle h, int k) {
+  if (h->fast3) {
+    const int e0 = h->ebase;
+    run_graph(h, 5000 + 2 * k + e0, [&] {
+      fast3_body(h, k, e0);
+      fast3_refine(h);
+    });
+    h->ebase = e0 ^ (k & 1);
+  } else {
+    run_graph(h, 3000 + k, [&] {
+      mixed_body<D>(h, k);
+      refine_residual<D>(h);
+    });
   }
 }
 
@@ -1377,7 +1424,29 @@ adafac_status adafac_solve(adafac_handle h, double rel_tol, int max_cycles, int*
   const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
   const int batch = mixed ? h->opt.inner_cycles : 8;
   int enq = 0;
-  bool done = false, diverged = false;
+  bool done = false, diverged = false, evaluated = false;
+  if (mixed && !h->batched) {
+    // residual first, then [cycles, u += e, residual] per step: the host
+    // reads each step's norm before it enqueues the next step
+    if (h->D == 2) enqueue_refine_only<2>(h);
+    else enqueue_refine_only<3>(h);
+    if ((st = read_ctl(h, &c)) != ADAFAC_OK) return st;
+    done = c.done != 0;
+    diverged = c.diverged != 0;
+    while (!done && !diverged && enq < max_cycles) {
+      const int k = max_cycles - enq < batch ? max_cycles - enq : batch;
+      if (h->D == 2) enqueue_solve_group<2>(h, k);
+      else enqueue_solve_group<3>(h, k);
+      enq += k;
+      if ((st = read_ctl(h, &c)) != ADAFAC_OK) return st;
+      done = c.done != 0;
+      diverged = c.diverged != 0;
+    }
+    // the last group ended with the residual of the final iterate
+    if (!done && !diverged) done = c.rel <= rel_tol;
+    evaluated = true;
+    enq = max_cycles;  // nothing below runs again
+  }
   while (enq < max_cycles) {
     const int k = max_cycles - enq < batch ? max_cycles - enq : batch;
     if (h->D == 2) enqueue_cycles<2>(h, k);
@@ -1388,7 +1457,7 @@ adafac_status adafac_solve(adafac_handle h, double rel_tol, int max_cycles, int*
     diverged = c.diverged != 0;
     if (done || diverged) break;
   }
-  if (!done && !diverged) {
+  if (!done && !diverged && !evaluated) {
     // residual of the final iterate, recorded like a cycle evaluation
     if (h->batched) {
       batch_step(h, 0);

@@ -339,7 +339,9 @@ __global__ void k_restrict_plain(LevelView<double> lf, LevelView<double> lc,
 // Norm of one residual evaluation: partial sums added in a fixed order.
 __global__ void k_norm_finalize(const double* __restrict__ partials, int nblocks, Control* ctl,
                                 double* __restrict__ hist, int hist_cap, int query) {
-  if (!query && (ctl->done || ctl->diverged)) return;
+  // a cycle evaluation after the end of the solve, or after a bounded wait
+  // gave up (its residual kernel returned at entry), records nothing
+  if (!query && (ctl->done || ctl->diverged || ctl->fault)) return;
   __shared__ double red[256];
   double acc = 0.0;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[i];
