@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "../../include/adafac.h"
+#include "adaptive_brick.h"
 #include "engine.h"
 
 namespace adafac {
@@ -368,6 +369,10 @@ struct adafac_adaptive_s {
   int npart = 0;
   double r0 = 0.0;
   std::vector<void*> allocs;
+  // the brick engine (adaptive_brick.h) runs the cycles when it covers the
+  // variant; the CSR arrays above are then not built
+  bool brick = false;
+  adafac::brick::System* bs = nullptr;
 };
 
 namespace adafac {
@@ -494,6 +499,23 @@ adafac_status build(adafac_adaptive h, const uint8_t* const* refine, const doubl
     }
   const int nn = (int)h->nodes.size();
   h->nn = nn;
+  if (h->brick) {
+    brick::Tree tree;
+    tree.exists = std::move(exists);
+    tree.cut = std::move(cut);
+    h->bs = new (std::nothrow) brick::System();
+    if (!h->bs) return ad_fail(h, ADAFAC_ERR_OOM, "brick engine: allocation failed");
+    std::string why;
+    const adafac_status st = brick::build(*h->bs, D, L, tree, eps, eps_scalar, f, h->stream, &why);
+    if (st != ADAFAC_OK) return ad_fail(h, st, why);
+    if (!dev_copy(h, &h->d_u, (const double*)nullptr, nn) ||
+        !dev_copy(h, &h->d_y, (const double*)nullptr, nn) ||
+        !dev_copy(h, &h->d_nodes, h->nodes.data(), h->nodes.size())) {
+      cudaGetLastError();
+      return ad_fail(h, ADAFAC_ERR_OOM, "device allocation or copy failed");
+    }
+    return ADAFAC_OK;
+  }
   // leaf stiffness (eps of a leaf cell: the mean of the fine cells it covers)
   // and lumped load (each corner of a leaf cell of width hc takes hc^D / 2^D f)
   struct Trip {
@@ -784,6 +806,16 @@ void enqueue_cycle(adafac_adaptive h) {
 
 // ||b - K u||_h over the nodal space's vertices (Eq. 10); synchronises
 adafac_status norm(adafac_adaptive h, double* out) {
+  if (h->brick) {
+    brick::enqueue_norm(*h->bs, h->stream);
+    brick::Ctl c;
+    if (cudaMemcpyAsync(&c, h->bs->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return ad_cuda(h, "norm");
+    *out = c.abs;
+    return ad_cuda(h, "norm");
+  }
   level_residuals(h, 1, false);
   int off = 0;
   std::vector<int> used;
@@ -811,6 +843,29 @@ void release(adafac_adaptive h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
+  if (h->bs) {
+    brick::release(*h->bs);
+    delete h->bs;
+    h->bs = nullptr;
+  }
+}
+
+// r0 of the brick engine's control block follows the host's
+adafac_status set_r0(adafac_adaptive h, double r0) {
+  h->r0 = r0;
+  if (!h->brick) return ADAFAC_OK;
+  if (cudaMemcpyAsync(&h->bs->ctl->r0, &h->r0, sizeof(double), cudaMemcpyHostToDevice,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return ad_cuda(h, "r0");
+  return ADAFAC_OK;
+}
+
+// the iterate at the leaf nodes (the brick engine gathers it from its levels)
+adafac_status sync_nodes(adafac_adaptive h) {
+  if (!h->brick) return ADAFAC_OK;
+  brick::gather_nodes(*h->bs, h->d_nodes, h->nn, h->d_u, h->stream);
+  return ad_cuda(h, "gather");
 }
 
 }  // namespace
@@ -843,8 +898,14 @@ adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* re
   h->L = depth;
   h->opt = *opt;
   h->stream = static_cast<cudaStream_t>(stream);
+  // the brick engine covers every variant but the exact R~ of Jac; path
+  // GENERIC keeps the CSR engine
+  h->brick = opt->path != ADAFAC_PATH_GENERIC &&
+             !(opt->variant == ADAFAC_VARIANT_JAC && opt->rtilde == ADAFAC_RTILDE_EXACT);
   adafac_status st = build(h, refine, eps, eps_is_scalar, f);
-  if (st == ADAFAC_OK) st = norm(h, &h->r0);
+  double r0 = 0.0;
+  if (st == ADAFAC_OK) st = norm(h, &r0);
+  if (st == ADAFAC_OK) st = set_r0(h, r0);
   if (st != ADAFAC_OK) {
     release(h);
     delete h;
@@ -857,7 +918,10 @@ adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* re
 adafac_status adafac_adaptive_cycle(adafac_adaptive h, int n_cycles) {
   using namespace adafac;
   if (!h || n_cycles < 0) return ADAFAC_ERR_INVALID_ARG;
-  for (int i = 0; i < n_cycles; ++i) enqueue_cycle(h);
+  for (int i = 0; i < n_cycles; ++i) {
+    if (h->brick) brick::enqueue_cycle(*h->bs, h->opt, false, h->stream);
+    else enqueue_cycle(h);
+  }
   return ad_cuda(h, "cycle");
 }
 
@@ -876,6 +940,54 @@ adafac_status adafac_adaptive_solve(adafac_adaptive h, double rel_tol, int max_c
                                     int* cycles_done, double* rel) {
   using namespace adafac;
   if (!h || max_cycles < 0) return ADAFAC_ERR_INVALID_ARG;
+  if (h->brick) {
+    // every cycle evaluates the norm of its residual first; the cycles after
+    // the one that meets rel_tol return at entry, and the host reads the
+    // control block after every batch of cycles
+    brick::Ctl c0;
+    if (cudaMemcpyAsync(&c0, h->bs->ctl, sizeof(c0), cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return ad_cuda(h, "solve");
+    brick::Ctl c = c0;
+    c.tol = rel_tol;
+    c.done = 0;
+    c.diverged = 0;
+    if (cudaMemcpyAsync(h->bs->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream) !=
+        cudaSuccess)
+      return ad_cuda(h, "solve");
+    int enq = 0;
+    while (enq < max_cycles && !c.done && !c.diverged) {
+      const int k = std::min(8, max_cycles - enq);
+      for (int i = 0; i < k; ++i) brick::enqueue_cycle(*h->bs, h->opt, true, h->stream);
+      enq += k;
+      if (cudaMemcpyAsync(&c, h->bs->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return ad_cuda(h, "solve");
+    }
+    const int applied = c.applied - c0.applied;
+    double r = c.rel;
+    if (!c.done && !c.diverged) {
+      // the norm of the final iterate
+      double a = 0.0;
+      adafac_status st = norm(h, &a);
+      if (st != ADAFAC_OK) return st;
+      r = h->r0 > 0.0 ? a / h->r0 : 0.0;
+    }
+    c.tol = -1.0;
+    c.done = 0;
+    if (cudaMemcpyAsync(&h->bs->ctl->tol, &c.tol, sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&h->bs->ctl->done, &c.done, sizeof(int), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return ad_cuda(h, "solve");
+    if (cycles_done) *cycles_done = applied;
+    if (rel) *rel = r;
+    if (c.diverged || !std::isfinite(r) || r > 1e6) return ADAFAC_ERR_DIVERGED;
+    return r <= rel_tol ? ADAFAC_OK : ADAFAC_ERR_NOT_CONVERGED;
+  }
   double r = 1.0;
   int c = 0;
   adafac_status st = adafac_adaptive_residual_norm(h, &r, nullptr);
@@ -902,6 +1014,8 @@ adafac_status adafac_adaptive_nodes(adafac_adaptive h, int64_t* idx, int64_t* co
 adafac_status adafac_adaptive_solution(adafac_adaptive h, double* dst) {
   using namespace adafac;
   if (!h || !dst) return ADAFAC_ERR_INVALID_ARG;
+  adafac_status st = sync_nodes(h);
+  if (st != ADAFAC_OK) return st;
   if (cudaMemcpyAsync(dst, h->d_u, sizeof(double) * h->nn, cudaMemcpyDeviceToHost, h->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -916,13 +1030,48 @@ adafac_status adafac_adaptive_set_solution(adafac_adaptive h, const double* src)
           cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return ad_cuda(h, "set solution");
-  return adafac_adaptive_residual_norm(h, nullptr, &h->r0);
+  if (h->brick) brick::scatter_nodes(*h->bs, h->d_nodes, h->nn, h->d_u, h->stream);
+  double r0 = 0.0;
+  adafac_status st = adafac_adaptive_residual_norm(h, nullptr, &r0);
+  if (st != ADAFAC_OK) return st;
+  return set_r0(h, r0);
 }
 
 adafac_status adafac_adaptive_level(adafac_adaptive h, int field, int level, double* dst,
                                     int64_t* count) {
   using namespace adafac;
   if (!h || !count || level < 1 || level > h->L) return ADAFAC_ERR_INVALID_ARG;
+  if (h->brick) {
+    // the level's bricks, read at its active vertices (1 / M_l > 0)
+    const brick::Level& bl = h->bs->lev[level];
+    if (field != ADAFAC_FIELD_ACTIVE && field != ADAFAC_FIELD_R && field != ADAFAC_FIELD_BT &&
+        field != ADAFAC_FIELD_G && field != ADAFAC_FIELD_INVDIAG)
+      return ADAFAC_ERR_INVALID_ARG;
+    std::vector<double> im(bl.V), vals;
+    const double* src = field == ADAFAC_FIELD_R ? bl.R
+                        : field == ADAFAC_FIELD_BT ? bl.BT
+                        : field == ADAFAC_FIELD_G ? bl.G
+                                                  : nullptr;
+    if (src) vals.assign(bl.V, 0.0);
+    if (cudaMemcpyAsync(im.data(), bl.IM, sizeof(double) * bl.V, cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess ||
+        (src && cudaMemcpyAsync(vals.data(), src, sizeof(double) * bl.V, cudaMemcpyDeviceToHost,
+                                h->stream) != cudaSuccess) ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return ad_cuda(h, "level field");
+    int64_t k = 0;
+    for (long long v = 0; v < bl.V; ++v) {
+      if (!(im[v] > 0.0)) continue;
+      if (dst) {
+        if (field == ADAFAC_FIELD_ACTIVE) dst[k] = (double)v;
+        else if (field == ADAFAC_FIELD_INVDIAG) dst[k] = im[v];
+        else dst[k] = vals.empty() ? 0.0 : vals[v];
+      }
+      ++k;
+    }
+    *count = k;
+    return ADAFAC_OK;
+  }
   ad::Level& lv = h->lev[level];
   if (field == ADAFAC_FIELD_ACTIVE) {
     *count = lv.na;
@@ -961,16 +1110,19 @@ adafac_status adafac_adaptive_level(adafac_adaptive h, int field, int level, dou
 adafac_status adafac_adaptive_transfer(adafac_adaptive dst, adafac_adaptive src) {
   using namespace adafac;
   if (!dst || !src || dst->D != src->D || dst->L != src->L) return ADAFAC_ERR_INVALID_ARG;
+  if (sync_nodes(src) != ADAFAC_OK) return ad_fail(dst, ADAFAC_ERR_CUDA, "transfer: source gather");
   if (src->stream && cudaStreamSynchronize(src->stream) != cudaSuccess)
     return ad_cuda(dst, "transfer: source stream");
-  // the source grid's leaf flags and node map, on the device once
-  if (!src->d_node_map) {
-    if (!dev_copy(src, &src->d_node_map, src->node_map.data(), src->node_map.size()) ||
-        !dev_copy(src, &src->d_leaf, src->leaf.data(), src->leaf.size()) ||
-        !dev_copy(src, &src->d_leaf_off, src->leaf_off.data(), src->leaf_off.size())) {
-      cudaGetLastError();
-      return ad_fail(dst, ADAFAC_ERR_OOM, "transfer: device allocation failed");
-    }
+  // the source grid's leaf flags and node map, on the device once (each on
+  // its own: a handle that was a transfer target already has its node map)
+  if ((!src->d_node_map &&
+       !dev_copy(src, &src->d_node_map, src->node_map.data(), src->node_map.size())) ||
+      (!src->d_leaf && !dev_copy(src, &src->d_leaf, src->leaf.data(), src->leaf.size())) ||
+      (!src->d_leaf_off &&
+       !dev_copy(src, &src->d_leaf_off, src->leaf_off.data(), src->leaf_off.size())) ||
+      !src->d_node_map || !src->d_leaf || !src->d_leaf_off) {
+    cudaGetLastError();
+    return ad_fail(dst, ADAFAC_ERR_OOM, "transfer: device allocation failed");
   }
   cudaStream_t s = dst->stream;
   const int nn = dst->nn;
@@ -987,6 +1139,16 @@ adafac_status adafac_adaptive_transfer(adafac_adaptive dst, adafac_adaptive src)
   // the function of the new space with those values at the nodal-space
   // vertices (zero Dirichlet data): level by level from the coarsest, each
   // level's pagodas add what the coarser ones left over at its vertices
+  if (dst->brick) {
+    if (!dst->d_node_map &&
+        !dev_copy(dst, &dst->d_node_map, dst->node_map.data(), dst->node_map.size())) {
+      cudaGetLastError();
+      return ad_fail(dst, ADAFAC_ERR_OOM, "transfer: device allocation failed");
+    }
+    brick::from_node_values(*dst->bs, dst->d_node_map, dst->d_y, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ad_cuda(dst, "transfer");
+    return set_r0(dst, src->r0);
+  }
   cudaMemsetAsync(dst->d_u, 0, sizeof(double) * nn, s);
   for (int l = 1; l <= dst->L; ++l) {
     ad::Level& lv = dst->lev[l];

@@ -224,3 +224,27 @@ def test_moving_band_solve_matches_the_oracle():
     np.testing.assert_allclose(rels, [h for _, h in hist], rtol=1e-8, atol=1e-14)
     _close(G.solution(), u_or, "iterate on the last tree")
     G.close()
+
+
+@pytest.mark.parametrize("tree,d,L", [("band", 2, 4), ("corner", 3, 3), ("band", 3, 3)])
+@pytest.mark.parametrize("variant", ["jac", "additive", "pi", "exp"])
+def test_brick_and_csr_engines_give_the_same_iterates(tree, d, L, variant):
+    # the brick engine (per-level grids; the default) and the CSR engine
+    # (pagoda matrices; path "generic") compute the same cycles in other
+    # summation orders
+    T, eps, f, S = _problem(tree, d, L)
+    u0 = _start(S)
+    out = {}
+    for path in ("auto", "generic"):
+        o = adafac.default_options(precision="fp64", variant=variant, omega_exp=0.7, path=path)
+        G = adafac.AdaptiveSolver(T.d, T.L, [T.refined[l] for l in range(1, T.L)], eps, f, o)
+        G.set_solution(u0)
+        G.cycle(3)
+        out[path] = (G.solution(), G.residual_norm(),
+                     [G.level("g", l) for l in range(1, L + 1)])
+        G.close()
+    _close(out["auto"][0], out["generic"][0], "brick vs CSR iterate", 1e-12)
+    assert out["auto"][1][1] == pytest.approx(out["generic"][1][1], rel=1e-12)
+    for l in range(L):
+        _close(out["auto"][2][l], out["generic"][2][l], f"g_{l + 1}", 1e-12,
+               scale=np.abs(out["generic"][2][l]).max() + 1e-300)
