@@ -448,7 +448,7 @@ adafac_status adafac_server_stats(adafac_server s, int* pending, int* running,
  * forgets every ticket.  Synchronises. */
 adafac_status adafac_server_destroy(adafac_server s);
 
-/* ---- Adaptive spacetrees (static trees, FP64) ---------------------------
+/* ---- Adaptive spacetrees (static trees; moving refinement by transfer) ---
  *
  * Sec. 2.1 and 2.3: level 1 exists in full (l_min = 1); a level-l cell that
  * exists is cut into 3^dim children where refine[l-1][cell] != 0 (l = 1 ..
@@ -473,16 +473,26 @@ adafac_status adafac_server_destroy(adafac_server s);
  *        NULL (zero)
  * Inputs are copied during the call.  The handle owns its device memory
  * (allocated here), runs on `stream` (cudaStream_t; NULL = legacy default).
- * Returns INVALID_ARG for a bad tree or options (precision MIXED, BoxMG
- * transfers and rediscretised coarse operators are regular-tree options),
- * OOM when an allocation fails. */
+ * Two engines compute the same cycles.  By default every level works on its
+ * full grid (the tiles of it that meet an existing cell): r_l is the chain
+ * rho_l = W_l + P^T rho_{l+1} of the levels' leaf-cell residuals W_l, the
+ * corrections return by T_l = g_l + P T_{l-1}, and M_l comes from the
+ * Galerkin element matrices collapsed level by level.  Path GENERIC, and the
+ * exact R~ of Jac, use Phi_l and K as sparse matrices instead.  Precision
+ * FP64 runs every step in FP64; MIXED (grid engine only) runs refinement
+ * steps: the FP64 leaf-cell residuals of every level and their norm, then
+ * inner_cycles FP32 cycles on the correction equation, then u += e in FP64.
+ * Returns INVALID_ARG for a bad tree or options (BoxMG transfers,
+ * rediscretised coarse operators and MIXED on the sparse-matrix engine are
+ * not available), OOM when an allocation fails. */
 typedef struct adafac_adaptive_s* adafac_adaptive;
 adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* refine,
                                     const double* eps, int eps_is_scalar, const double* f,
                                     const adafac_options* opt, void* stream,
                                     adafac_adaptive* out);
 
-/* Enqueues n_cycles >= 0 cycles (Eq. 9 on the generating system).  Asynchronous. */
+/* Enqueues n_cycles >= 0 cycles (Eq. 9 on the generating system; MIXED:
+ * refinement steps of at most inner_cycles cycles).  Asynchronous. */
 adafac_status adafac_adaptive_cycle(adafac_adaptive h, int n_cycles);
 
 /* Eq. 10 over the vertices of the nodal space (every position that is an
@@ -493,7 +503,10 @@ adafac_status adafac_adaptive_cycle(adafac_adaptive h, int n_cycles);
 adafac_status adafac_adaptive_residual_norm(adafac_adaptive h, double* rel, double* abs);
 
 /* Cycles until the normalised residual is <= rel_tol or max_cycles cycles ran;
- * NOT_CONVERGED / DIVERGED as adafac_solve.  Synchronises every cycle. */
+ * NOT_CONVERGED / DIVERGED as adafac_solve.  The grid engine tests the norm
+ * on the device before every cycle (MIXED: before every refinement step)
+ * and synchronises after every 8 cycles (MIXED: every step); the sparse-matrix
+ * engine synchronises every cycle. */
 adafac_status adafac_adaptive_solve(adafac_adaptive h, double rel_tol, int max_cycles,
                                     int* cycles_done, double* rel);
 

@@ -437,7 +437,8 @@ class Server:
 
 
 class AdaptiveSolver:
-    """adAFAC on a static adaptive spacetree (FP64; adafac_adaptive_*).
+    """adAFAC on a static adaptive spacetree (adafac_adaptive_*; FP64, or
+    MIXED refinement steps on the per-level grid engine).
 
     ``refine``: for l = 1 .. depth-1 an array of shape (3^l,)*dim (array axis
     order, the last axis is x) whose non-zero entries cut existing level-l

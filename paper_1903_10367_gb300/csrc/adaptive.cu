@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -373,6 +374,10 @@ struct adafac_adaptive_s {
   // variant; the CSR arrays above are then not built
   bool brick = false;
   adafac::brick::System* bs = nullptr;
+  // CUDA graphs of the brick engine's batches (key: kind, cycles, norm)
+  std::map<long, cudaGraphExec_t> graphs;
+  cudaStream_t cap = nullptr;
+  bool use_graphs = true;
 };
 
 namespace adafac {
@@ -506,7 +511,9 @@ adafac_status build(adafac_adaptive h, const uint8_t* const* refine, const doubl
     h->bs = new (std::nothrow) brick::System();
     if (!h->bs) return ad_fail(h, ADAFAC_ERR_OOM, "brick engine: allocation failed");
     std::string why;
-    const adafac_status st = brick::build(*h->bs, D, L, tree, eps, eps_scalar, f, h->stream, &why);
+    const bool mixed = h->opt.precision == ADAFAC_PRECISION_MIXED;
+    const adafac_status st =
+        brick::build(*h->bs, D, L, tree, eps, eps_scalar, f, mixed, h->stream, &why);
     if (st != ADAFAC_OK) return ad_fail(h, st, why);
     if (!dev_copy(h, &h->d_u, (const double*)nullptr, nn) ||
         !dev_copy(h, &h->d_y, (const double*)nullptr, nn) ||
@@ -848,6 +855,49 @@ void release(adafac_adaptive h) {
     delete h->bs;
     h->bs = nullptr;
   }
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  if (h->cap) cudaStreamDestroy(h->cap);
+  h->cap = nullptr;
+}
+
+// Replays `enqueue` (launches on the stream it is given) as a CUDA graph
+// captured once per key; launches directly when capture is unavailable.
+template <typename F>
+void run_graph(adafac_adaptive h, long key, F&& enqueue) {
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaGraphExec_t ex = nullptr;
+    bool ok = h->use_graphs &&
+              (h->cap || cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess);
+    if (ok) ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      enqueue(h->cap);
+      cudaGraph_t g = nullptr;
+      ok = cudaStreamEndCapture(h->cap, &g) == cudaSuccess &&
+           cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+    }
+    if (!ok) {
+      cudaGetLastError();
+      h->use_graphs = false;
+      enqueue(h->stream);
+      return;
+    }
+    it = h->graphs.emplace(key, ex).first;
+  }
+  cudaGraphLaunch(it->second, h->stream);
+}
+
+// brick engine: n FP64 cycles, or a refinement step of n cycles (MIXED)
+void brick_batch(adafac_adaptive h, int n, bool with_norm) {
+  const bool mixed = h->bs->mixed;
+  const long key = ((long)n << 2) | (with_norm ? 2 : 0) | (mixed ? 1 : 0);
+  run_graph(h, key, [&](cudaStream_t s) {
+    if (mixed) brick::enqueue_step(*h->bs, h->opt, n, with_norm, s);
+    else
+      for (int i = 0; i < n; ++i) brick::enqueue_cycle(*h->bs, h->opt, with_norm, s);
+  });
 }
 
 // r0 of the brick engine's control block follows the host's
@@ -883,7 +933,13 @@ adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* re
   if ((dim != 2 && dim != 3) || depth < 1 || !opt || !eps || (depth > 1 && !refine))
     return ADAFAC_ERR_INVALID_ARG;
   if (ipow(ipow(3, depth) + 1, dim) > (1LL << 31) - 1) return ADAFAC_ERR_INVALID_ARG;
-  if (opt->precision != ADAFAC_PRECISION_FP64 || opt->transfer != ADAFAC_TRANSFER_DLINEAR ||
+  const bool brick_engine =
+      opt->path != ADAFAC_PATH_GENERIC &&
+      !(opt->variant == ADAFAC_VARIANT_JAC && opt->rtilde == ADAFAC_RTILDE_EXACT);
+  // MIXED precision (FP32 cycles, FP64 refinement steps) runs on the brick engine
+  if ((opt->precision != ADAFAC_PRECISION_FP64 &&
+       !(opt->precision == ADAFAC_PRECISION_MIXED && brick_engine)) ||
+      opt->inner_cycles < 1 || opt->transfer != ADAFAC_TRANSFER_DLINEAR ||
       opt->coarse_op != ADAFAC_COARSE_GALERKIN || opt->variant < 0 || opt->variant > 3 ||
       opt->lmin < 1 || opt->lmin > depth || !(opt->omega > 0.0) || !(opt->omega_tilde > 0.0))
     return ADAFAC_ERR_INVALID_ARG;
@@ -900,8 +956,7 @@ adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* re
   h->stream = static_cast<cudaStream_t>(stream);
   // the brick engine covers every variant but the exact R~ of Jac; path
   // GENERIC keeps the CSR engine
-  h->brick = opt->path != ADAFAC_PATH_GENERIC &&
-             !(opt->variant == ADAFAC_VARIANT_JAC && opt->rtilde == ADAFAC_RTILDE_EXACT);
+  h->brick = brick_engine;
   adafac_status st = build(h, refine, eps, eps_is_scalar, f);
   double r0 = 0.0;
   if (st == ADAFAC_OK) st = norm(h, &r0);
@@ -918,6 +973,17 @@ adafac_status adafac_adaptive_setup(int dim, int depth, const uint8_t* const* re
 adafac_status adafac_adaptive_cycle(adafac_adaptive h, int n_cycles) {
   using namespace adafac;
   if (!h || n_cycles < 0) return ADAFAC_ERR_INVALID_ARG;
+  if (h->brick) {
+    // FP64: one graph of the n cycles; MIXED: refinement steps of
+    // inner_cycles FP32 cycles
+    const int batch = h->bs->mixed ? h->opt.inner_cycles : n_cycles;
+    for (int done = 0; done < n_cycles;) {
+      const int k = std::min(batch, n_cycles - done);
+      brick_batch(h, k, false);
+      done += k;
+    }
+    return ad_cuda(h, "cycle");
+  }
   for (int i = 0; i < n_cycles; ++i) {
     if (h->brick) brick::enqueue_cycle(*h->bs, h->opt, false, h->stream);
     else enqueue_cycle(h);
@@ -957,9 +1023,10 @@ adafac_status adafac_adaptive_solve(adafac_adaptive h, double rel_tol, int max_c
         cudaSuccess)
       return ad_cuda(h, "solve");
     int enq = 0;
+    const bool mixed = h->bs->mixed;
     while (enq < max_cycles && !c.done && !c.diverged) {
-      const int k = std::min(8, max_cycles - enq);
-      for (int i = 0; i < k; ++i) brick::enqueue_cycle(*h->bs, h->opt, true, h->stream);
+      const int k = std::min(mixed ? h->opt.inner_cycles : 8, max_cycles - enq);
+      brick_batch(h, k, true);
       enq += k;
       if (cudaMemcpyAsync(&c, h->bs->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream) !=
               cudaSuccess ||

@@ -23,19 +23,20 @@ namespace {
 
 constexpr int kT = kTX * kTY;  // threads per tile block
 
+// the truncated smoothed-restriction stencil in the cycle's arithmetic type
+template <typename T>
 struct Stencil5 {
-  double w[125];
+  T w[125];
 };
 
-// the level's vertex (x, y, z) of this thread in tile `tile`; false outside
+// the level's vertex (x, y, z) of this thread in a tile (x: tile column |
+// tile row << 16, y: plane); false outside the grid
 template <int D>
-__device__ __forceinline__ bool tile_vertex(const Level& lv, int tile, int* c) {
-  const int np1 = lv.n + 1;
-  const int ntx = (np1 + kTX - 1) / kTX, nty = (np1 + kTY - 1) / kTY;
-  const int tx = tile % ntx, rest = tile / ntx;
-  c[0] = tx * kTX + (int)(threadIdx.x % kTX);
-  c[1] = (rest % nty) * kTY + (int)(threadIdx.x / kTX);
-  c[2] = D == 3 ? rest / nty : 0;
+__device__ __forceinline__ bool tile_vertex(int n, int2 tile, int* c) {
+  const int np1 = n + 1;
+  c[0] = (tile.x & 0xffff) * kTX + (int)(threadIdx.x % kTX);
+  c[1] = (tile.x >> 16) * kTY + (int)(threadIdx.x / kTX);
+  c[2] = D == 3 ? tile.y : 0;
   return c[0] < np1 && c[1] < np1;
 }
 
@@ -67,35 +68,55 @@ __device__ __forceinline__ double block_sum(double a) {
   return s;
 }
 
-// W_l at an interior vertex: the lumped load of the level's leaf cells minus
-// their element matrices applied to U_l (eps of a non-leaf cell is 0 there).
+// The arrays of one level a cycle works on, in its arithmetic type: the FP64
+// iterate U_l and its chains, or in a mixed solve the FP32 correction E_l
+// with the FP32 right-hand sides of the level's leaf cells.
+template <typename T>
+struct View {
+  int n = 0;
+  T* U = nullptr;         // iterate (or correction) on the level's grid
+  T* R = nullptr;         // rho_l (mixed: the chain of -K e, added to R0)
+  const T* R0 = nullptr;  // mixed: the step's FP64 rho_l rounded to FP32
+  T* G = nullptr;         // g_l
+  T* Tc = nullptr;        // T_l (null on the finest level)
+  const T* IM = nullptr;  // 1 / M_l at active vertices, else 0
+  const T* B = nullptr;   // load of the level's leaf cells (null: zero)
+  T* BT = nullptr;        // b~_l (optional)
+  const T* EL = nullptr;  // eps of the level's leaf cells, else 0
+  const uint8_t* nodal = nullptr;
+  const int2* tiles = nullptr;
+  int part_off = 0;
+};
+
+// W_l at an interior vertex: the load of the level's leaf cells minus their
+// element matrices applied to U_l (eps of a non-leaf cell is 0 there).
 // d-linear element by the Hamming distance of two corners (Sec. 2.1):
 // 2-D 2/3, -1/6, -1/3; 3-D 1/3, 0, -1/12, -1/12, times h^(D-2).
-template <int D>
-__device__ __forceinline__ double leaf_residual(const Level& lv, const int* c, long long v) {
+template <int D, typename T>
+__device__ __forceinline__ T leaf_residual(const View<T>& lv, const int* c, long long v) {
   const int n = lv.n, np1 = n + 1;
-  const double* __restrict__ U = lv.U;
-  const double* __restrict__ e = lv.EL;
+  const T* __restrict__ U = lv.U;
+  const T* __restrict__ e = lv.EL;
   if (D == 2) {
-    double E[9];
+    T E[9];
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) E[(dy + 1) * 3 + dx + 1] = U[v + dy * np1 + dx];
     const long long c0 = (long long)(c[1] - 1) * n + c[0] - 1;
-    double Ax = 0.0;
+    T Ax = T(0);
 #pragma unroll
     for (int sy = 0; sy < 2; ++sy)
 #pragma unroll
       for (int sx = 0; sx < 2; ++sx) {
-        const double ec = e[c0 + sy * n + sx];
-        const double near = E[3 + 2 * sx] + E[6 * sy + 1];
-        Ax += ec * ((2.0 / 3.0) * E[4] + (-1.0 / 6.0) * near + (-1.0 / 3.0) * E[6 * sy + 2 * sx]);
+        const T ec = e[c0 + sy * n + sx];
+        const T near = E[3 + 2 * sx] + E[6 * sy + 1];
+        Ax += ec * (T(2.0 / 3.0) * E[4] + T(-1.0 / 6.0) * near + T(-1.0 / 3.0) * E[6 * sy + 2 * sx]);
       }
-    return lv.B[v] - Ax;
+    return (lv.B ? lv.B[v] : T(0)) - Ax;
   } else {
     const long long P = (long long)np1 * np1;
-    double E[3][9];
+    T E[3][9];
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
@@ -103,117 +124,124 @@ __device__ __forceinline__ double leaf_residual(const Level& lv, const int* c, l
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx)
           E[dz + 1][(dy + 1) * 3 + dx + 1] = U[v + dz * P + dy * np1 + dx];
-    double esum = 0.0, far = 0.0;
+    T esum = T(0), far = T(0);
 #pragma unroll
     for (int sz = 0; sz < 2; ++sz) {
-      const double* S = E[2 * sz];
+      const T* S = E[2 * sz];
       const long long cz = (long long)(c[2] - 1 + sz) * n;
 #pragma unroll
       for (int sy = 0; sy < 2; ++sy)
 #pragma unroll
         for (int sx = 0; sx < 2; ++sx) {
-          const double ec = e[(cz + c[1] - 1 + sy) * n + c[0] - 1 + sx];
-          const double f = (E[1][6 * sy + 2 * sx] + S[3 + 2 * sx]) + (S[6 * sy + 1] + S[6 * sy + 2 * sx]);
+          const T ec = e[(cz + c[1] - 1 + sy) * n + c[0] - 1 + sx];
+          const T f = (E[1][6 * sy + 2 * sx] + S[3 + 2 * sx]) + (S[6 * sy + 1] + S[6 * sy + 2 * sx]);
           esum += ec;
           far += ec * f;
         }
     }
-    const double h = 1.0 / (double)n;
-    return lv.B[v] - h * ((1.0 / 3.0) * E[1][4] * esum + (-1.0 / 12.0) * far);
+    const T h = T(1.0 / (double)n);
+    return (lv.B ? lv.B[v] : T(0)) - h * (T(1.0 / 3.0) * E[1][4] * esum + T(-1.0 / 12.0) * far);
   }
 }
 
 // d-linear weight of offset o in [-2, 2] of the 3:1 restriction
-__device__ __forceinline__ double wrest(int o) {
-  return o == 0 ? 1.0 : (o == 1 || o == -1 ? 2.0 / 3.0 : 1.0 / 3.0);
+template <typename T>
+__device__ __forceinline__ T wrest(int o) {
+  return o == 0 ? T(1) : (o == 1 || o == -1 ? T(2.0 / 3.0) : T(1.0 / 3.0));
 }
 
-// rho_l = W_l + P^T rho_{l+1} at the tile's vertices, zero on the boundary;
-// partial of h^D rho^2 over the nodal-space vertices of the block's tile
 template <int D>
+__device__ __forceinline__ long long fine_of(const int* c, int nf1) {
+  return D == 2 ? (long long)(3 * c[1]) * nf1 + 3 * c[0]
+                : ((long long)(3 * c[2]) * nf1 + 3 * c[1]) * nf1 + 3 * c[0];
+}
+
+// rho_l = W_l + P^T rho_{l+1} at the tile's vertices, zero on the boundary.
+// With part: partial of h^D rho^2 over the nodal-space vertices of the
+// block's tile.
+template <int D, typename T>
 __global__ void __launch_bounds__(kT)
-    k_br_residual(const Level lv, const Level fine, double hD, double* __restrict__ part,
+    k_br_residual(const View<T> lv, const View<T> fine, double hD, double* __restrict__ part,
                   const Ctl* ctl, int query) {
   if (!query && halted(ctl)) return;
   int c[3];
-  const bool in = tile_vertex<D>(lv, lv.tiles[blockIdx.x], c);
+  const bool in = tile_vertex<D>(lv.n, lv.tiles[blockIdx.x], c);
   double acc = 0.0;
   if (in) {
     const int n = lv.n, np1 = n + 1;
     const long long v = vidx<D>(c, np1);
-    double rho = 0.0;
+    T rho = T(0);
     if (inner<D>(c, n)) {
-      rho = leaf_residual<D>(lv, c, v);
+      rho = leaf_residual<D, T>(lv, c, v);
       if (fine.n) {
         const int nf1 = fine.n + 1;
-        const long long f0 = D == 2 ? (long long)(3 * c[1]) * nf1 + 3 * c[0]
-                                    : ((long long)(3 * c[2]) * nf1 + 3 * c[1]) * nf1 + 3 * c[0];
-        double rs = 0.0;
+        const long long f0 = fine_of<D>(c, nf1);
+        T rs = T(0);
         constexpr int OZ = D == 3 ? 2 : 0;
         for (int oz = -OZ; oz <= OZ; ++oz) {
-          double ry = 0.0;
+          T ry = T(0);
 #pragma unroll
           for (int oy = -2; oy <= 2; ++oy) {
             const long long row = f0 + ((long long)oz * nf1 + oy) * nf1;
-            double rx = 0.0;
+            T rx = T(0);
 #pragma unroll
-            for (int ox = -2; ox <= 2; ++ox) rx += wrest(ox) * fine.R[row + ox];
-            ry += wrest(oy) * rx;
+            for (int ox = -2; ox <= 2; ++ox) rx += wrest<T>(ox) * fine.R[row + ox];
+            ry += wrest<T>(oy) * rx;
           }
-          rs += wrest(oz) * ry;
+          rs += wrest<T>(oz) * ry;
         }
         rho += rs;
       }
-      if (lv.nodal[v]) acc = rho * rho;
+      if (part && lv.nodal[v]) acc = (double)rho * (double)rho;
     }
     lv.R[v] = rho;
   }
-  const double s = block_sum(acc);
-  if (threadIdx.x == 0) part[lv.part_off + blockIdx.x] = s * hD;
+  if (part) {
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0) part[lv.part_off + blockIdx.x] = sum * hD;
+  }
 }
 
 // g_l at the tile's vertices (zero where the vertex is not active)
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(kT)
-    k_br_correct(const Level lv, const Level fine, const Stencil5 st, int variant, double omega,
+    k_br_correct(const View<T> lv, const View<T> fine, const Stencil5<T> st, int variant, double omega,
                  double omega_t, double gscale, const Ctl* ctl) {
   if (halted(ctl)) return;
   int c[3];
-  if (!tile_vertex<D>(lv, lv.tiles[blockIdx.x], c)) return;
+  if (!tile_vertex<D>(lv.n, lv.tiles[blockIdx.x], c)) return;
   const int np1 = lv.n + 1;
   const long long v = vidx<D>(c, np1);
-  const double im = lv.IM[v];
-  double g = 0.0, bt = 0.0;
-  if (im > 0.0) {
-    const double cl = omega * lv.R[v] * im;
+  const T im = lv.IM[v];
+  const T om = T(omega);
+  T g = T(0), bt = T(0);
+  if (im > T(0)) {
+    const T cl = om * (lv.R[v] + (lv.R0 ? lv.R0[v] : T(0))) * im;
     if (fine.n && variant == ADAFAC_VARIANT_JAC) {
       // b~_l = omega S~ r_{l+1} over the 5^D window, r_{l+1} zero where the
       // finer level's vertex is not active
       const int nf1 = fine.n + 1;
-      const long long f0 = D == 2 ? (long long)(3 * c[1]) * nf1 + 3 * c[0]
-                                  : ((long long)(3 * c[2]) * nf1 + 3 * c[1]) * nf1 + 3 * c[0];
+      const long long f0 = fine_of<D>(c, nf1);
       constexpr int OZ = D == 3 ? 2 : 0;
-      double acc = 0.0;
+      T acc = T(0);
       for (int oz = -OZ; oz <= OZ; ++oz)
 #pragma unroll
         for (int oy = -2; oy <= 2; ++oy)
 #pragma unroll
           for (int ox = -2; ox <= 2; ++ox) {
             const long long f = f0 + ((long long)oz * nf1 + oy) * nf1 + ox;
-            const double r = fine.IM[f] > 0.0 ? fine.R[f] : 0.0;
+            const T r = fine.IM[f] > T(0) ? fine.R[f] + (fine.R0 ? fine.R0[f] : T(0)) : T(0);
             acc += st.w[((oz + OZ) * 5 + oy + 2) * 5 + ox + 2] * r;
           }
-      bt = omega * acc;
-      g = cl - omega_t * bt * im;
+      bt = om * acc;
+      g = cl - T(omega_t) * bt * im;
     } else if (fine.n && variant == ADAFAC_VARIANT_PI) {
       // minus the finer level's correction at the coinciding vertex (I c_{l+1})
-      const int nf1 = fine.n + 1;
-      const long long f = D == 2 ? (long long)(3 * c[1]) * nf1 + 3 * c[0]
-                                 : ((long long)(3 * c[2]) * nf1 + 3 * c[1]) * nf1 + 3 * c[0];
-      const double imf = fine.IM[f];
-      g = cl - (imf > 0.0 ? omega * fine.R[f] * imf : 0.0);
+      const long long f = fine_of<D>(c, fine.n + 1);
+      const T imf = fine.IM[f];
+      g = cl - (imf > T(0) ? om * (fine.R[f] + (fine.R0 ? fine.R0[f] : T(0))) * imf : T(0));
     } else {
-      g = gscale * cl;
+      g = T(gscale) * cl;
     }
   }
   lv.G[v] = g;
@@ -222,20 +250,20 @@ __global__ void __launch_bounds__(kT)
 
 // T_l = g_l + P T_{l-1} (coarse.n == 0 on the coarsest level of the cycle);
 // U_l += T_l
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(kT)
-    k_br_prolong(const Level lv, const Level coarse, Ctl* ctl, int count) {
+    k_br_prolong(const View<T> lv, const View<T> coarse, Ctl* ctl, int count) {
   if (halted(ctl)) return;
   if (count && blockIdx.x == 0 && threadIdx.x == 0) ctl->applied += 1;
   int c[3];
-  if (!tile_vertex<D>(lv, lv.tiles[blockIdx.x], c)) return;
+  if (!tile_vertex<D>(lv.n, lv.tiles[blockIdx.x], c)) return;
   const int n = lv.n, np1 = n + 1;
   const long long v = vidx<D>(c, np1);
   if (!inner<D>(c, n)) {
-    if (lv.T) lv.T[v] = 0.0;
+    if (lv.Tc) lv.Tc[v] = T(0);
     return;
   }
-  double t = lv.G[v];
+  T t = lv.G[v];
   if (coarse.n) {
     const int nc = coarse.n, ncp1 = nc + 1;
     int O[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
@@ -244,28 +272,53 @@ __global__ void __launch_bounds__(kT)
       O[j] = min(c[j] / 3, nc - 1);
       lo[j] = c[j] - 3 * O[j];
     }
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int e = 0; e < (1 << D); ++e) {
       bool zero = false;
-      double w = 1.0;
+      T w = T(1);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         const int bit = (e >> j) & 1;
         zero = zero || (bit && lo[j] == 0);
-        const double tt = lo[j] == 0 ? 0.0 : (lo[j] == 1 ? 1.0 / 3.0 : 2.0 / 3.0);
-        w *= bit ? tt : 1.0 - tt;
+        const T tt = lo[j] == 0 ? T(0) : (lo[j] == 1 ? T(1.0 / 3.0) : T(2.0 / 3.0));
+        w *= bit ? tt : T(1) - tt;
       }
       if (zero) continue;
       const int ex = e & 1, ey = (e >> 1) & 1, ez = (e >> 2) & 1;
       const long long cv = D == 2 ? (long long)(O[1] + ey) * ncp1 + O[0] + ex
                                   : ((long long)(O[2] + ez) * ncp1 + O[1] + ey) * ncp1 + O[0] + ex;
-      acc += w * coarse.T[cv];
+      acc += w * coarse.Tc[cv];
     }
     t += acc;
   }
-  if (lv.T) lv.T[v] = t;
+  if (lv.Tc) lv.Tc[v] = t;
   lv.U[v] += t;
+}
+
+// mixed solve: the step's FP64 rho_l rounded to FP32, over the level's tiles
+template <int D>
+__global__ void __launch_bounds__(kT)
+    k_br_round(int n, const int2* __restrict__ tiles, const double* __restrict__ R,
+               float* __restrict__ R32, const Ctl* ctl) {
+  if (halted(ctl)) return;
+  int c[3];
+  if (!tile_vertex<D>(n, tiles[blockIdx.x], c)) return;
+  const long long v = vidx<D>(c, n + 1);
+  R32[v] = (float)R[v];
+}
+
+// mixed solve: U_l += E_l (FP64 += FP32), E_l = 0, over the level's tiles
+template <int D>
+__global__ void __launch_bounds__(kT)
+    k_br_add_correction(int n, const int2* __restrict__ tiles, double* __restrict__ U,
+                        float* __restrict__ E, const Ctl* ctl) {
+  if (halted(ctl)) return;
+  int c[3];
+  if (!tile_vertex<D>(n, tiles[blockIdx.x], c)) return;
+  const long long v = vidx<D>(c, n + 1);
+  U[v] += (double)E[v];
+  E[v] = 0.f;
 }
 
 // the norm of Eq. 10 from the partials (fixed order); in a solve, the test
@@ -481,6 +534,13 @@ __global__ void k_br_nodal(int n, const double* __restrict__ IM, const double* _
   }
 }
 
+// FP32 copies of 1 / M_l and eps for the cycles of a mixed solve
+__global__ void k_br_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
 // ---- leaf-node vectors -------------------------------------------------------------
 
 template <int D>
@@ -551,7 +611,7 @@ __global__ void __launch_bounds__(kT)
     k_br_from_values(const Level lv, const Level coarse, int L, int N1, const int* __restrict__ node_map,
                      const double* __restrict__ vals) {
   int c[3];
-  if (!tile_vertex<D>(lv, lv.tiles[blockIdx.x], c)) return;
+  if (!tile_vertex<D>(lv.n, lv.tiles[blockIdx.x], c)) return;
   const int n = lv.n, np1 = n + 1;
   const long long v = vidx<D>(c, np1);
   double t = 0.0;
@@ -624,9 +684,10 @@ void release(System& S) {
 }
 
 adafac_status build(System& S, int D, int L, const Tree& tree, const double* eps, int eps_scalar,
-                    const double* f, cudaStream_t s, std::string* err) {
+                    const double* f, bool mixed, cudaStream_t s, std::string* err) {
   S.D = D;
   S.L = L;
+  S.mixed = mixed;
   const int NC = 1 << D;
   const long long N = ipw(3, L), N1 = N + 1;
   auto fail = [&](const char* what) {
@@ -658,14 +719,17 @@ adafac_status build(System& S, int D, int L, const Tree& tree, const double* eps
         mark[((size_t)z * nty + y / kTY) * ntx + x / kTX] = 1;
       }
     }
-    std::vector<int> tiles;
+    std::vector<int2> tiles;
     for (size_t t = 0; t < mark.size(); ++t)
-      if (mark[t]) tiles.push_back((int)t);
+      if (mark[t]) {
+        const int tx = (int)(t % ntx), ty = (int)((t / ntx) % nty), tz = (int)(t / ntx / nty);
+        tiles.push_back(make_int2(tx | (ty << 16), tz));
+      }
     lv.ntiles = (int)tiles.size();
     lv.part_off = part;
     part += lv.ntiles;
     lv.leaf = dalloc<uint8_t>(S, lv.C);
-    lv.tiles = dalloc<int>(S, lv.ntiles);
+    lv.tiles = dalloc<int2>(S, lv.ntiles);
     lv.U = dalloc<double>(S, lv.V);
     lv.R = dalloc<double>(S, lv.V);
     lv.G = dalloc<double>(S, lv.V);
@@ -677,11 +741,22 @@ adafac_status build(System& S, int D, int L, const Tree& tree, const double* eps
       lv.T = dalloc<double>(S, lv.V);
       lv.BT = dalloc<double>(S, lv.V);
     }
+    if (mixed) {
+      lv.E32 = dalloc<float>(S, lv.V);
+      lv.R32 = dalloc<float>(S, lv.V);
+      lv.G32 = dalloc<float>(S, lv.V);
+      lv.IM32 = dalloc<float>(S, lv.V);
+      lv.RHS32 = dalloc<float>(S, lv.V);
+      lv.EL32 = dalloc<float>(S, lv.C);
+      if (l < L) lv.T32 = dalloc<float>(S, lv.V);
+      if (!lv.E32 || !lv.R32 || !lv.G32 || !lv.IM32 || !lv.RHS32 || !lv.EL32 || (l < L && !lv.T32))
+        return fail("brick engine: device allocation failed");
+    }
     if (!lv.leaf || !lv.tiles || !lv.U || !lv.R || !lv.G || !lv.IM || !lv.B || !lv.EL ||
         !lv.nodal || (l < L && (!lv.T || !lv.BT)))
       return fail("brick engine: device allocation failed");
     if (cudaMemcpyAsync(lv.leaf, state.data(), lv.C, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        (lv.ntiles && cudaMemcpyAsync(lv.tiles, tiles.data(), sizeof(int) * tiles.size(),
+        (lv.ntiles && cudaMemcpyAsync(lv.tiles, tiles.data(), sizeof(int2) * tiles.size(),
                                       cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return fail("brick engine: copy of the tree failed");
@@ -781,6 +856,13 @@ adafac_status build(System& S, int D, int L, const Tree& tree, const double* eps
     if (D == 2) k_br_nodal<2><<<grid_for(lv.V), kT, 0, s>>>(lv.n, lv.IM, IMf, lv.nodal);
     else k_br_nodal<3><<<grid_for(lv.V), kT, 0, s>>>(lv.n, lv.IM, IMf, lv.nodal);
   }
+  if (mixed) {
+    for (int l = 1; l <= L; ++l) {
+      Level& lv = S.lev[l];
+      k_br_to_float<<<grid_for(lv.V), kT, 0, s>>>(lv.V, lv.IM, lv.IM32);
+      k_br_to_float<<<grid_for(lv.C), kT, 0, s>>>(lv.C, lv.EL, lv.EL32);
+    }
+  }
   smoothed_restriction_stencil(D, S.stilde);
   Ctl c{};
   c.tol = -1.0;
@@ -792,35 +874,82 @@ adafac_status build(System& S, int D, int L, const Tree& tree, const double* eps
 
 namespace {
 
-Level none() { return Level(); }
+template <typename T>
+View<T> none() {
+  return View<T>();
+}
 
-template <int D>
-void residual_chain(System& S, int lmin, bool query, cudaStream_t s) {
-  for (int l = S.L; l >= lmin; --l) {
+View<double> view64(const Level& lv) {
+  View<double> v;
+  v.n = lv.n;
+  v.U = lv.U;
+  v.R = lv.R;
+  v.G = lv.G;
+  v.Tc = lv.T;
+  v.IM = lv.IM;
+  v.B = lv.B;
+  v.BT = lv.BT;
+  v.EL = lv.EL;
+  v.nodal = lv.nodal;
+  v.tiles = lv.tiles;
+  v.part_off = lv.part_off;
+  return v;
+}
+
+View<float> view32(const Level& lv) {
+  View<float> v;
+  v.n = lv.n;
+  v.U = lv.E32;
+  v.R = lv.R32;
+  v.G = lv.G32;
+  v.Tc = lv.T32;
+  v.IM = lv.IM32;
+  v.R0 = lv.RHS32;
+  v.EL = lv.EL32;
+  v.nodal = lv.nodal;
+  v.tiles = lv.tiles;
+  v.part_off = lv.part_off;
+  return v;
+}
+
+template <typename T>
+View<T> view(const Level& lv);
+template <>
+View<double> view<double>(const Level& lv) {
+  return view64(lv);
+}
+template <>
+View<float> view<float>(const Level& lv) {
+  return view32(lv);
+}
+
+// the residual chain of levels L .. lo; FP64 with the norm partials (and,
+// in a mixed solve, the FP32 right-hand sides), FP32 without
+template <int D, typename T>
+void residual_chain(System& S, int lo, bool query, bool partials, cudaStream_t s) {
+  for (int l = S.L; l >= lo; --l) {
     Level& lv = S.lev[l];
     if (!lv.ntiles) continue;
-    const Level fine = l < S.L ? S.lev[l + 1] : none();
+    const View<T> fine = l < S.L ? view<T>(S.lev[l + 1]) : none<T>();
     const double hD = std::pow(1.0 / (double)lv.n, D);
-    k_br_residual<D><<<lv.ntiles, kT, 0, s>>>(lv, fine, hD, S.part, S.ctl, query ? 1 : 0);
+    k_br_residual<D, T><<<lv.ntiles, kT, 0, s>>>(view<T>(lv), fine, hD, partials ? S.part : nullptr,
+                                                S.ctl, query ? 1 : 0);
   }
 }
 
-template <int D>
-void cycle_d(System& S, const adafac_options& o, bool with_norm, cudaStream_t s) {
+// corrections and prolongation of one cycle over levels lmin .. L
+template <int D, typename T>
+void corrections(System& S, const adafac_options& o, cudaStream_t s) {
   const int L = S.L, lmin = o.lmin;
-  // the norm runs over every level's nodal-space vertices: the chain goes to
-  // level 1 when it is evaluated
-  residual_chain<D>(S, with_norm ? 1 : lmin, false, s);
-  if (with_norm) k_br_finalize<<<1, kT, 0, s>>>(S.part, S.npart, S.ctl, 0);
-  Stencil5 st;
-  std::memcpy(st.w, S.stilde, sizeof(st.w));
+  Stencil5<T> st;
+  for (int k = 0; k < 125; ++k) st.w[k] = (T)S.stilde[k];
   for (int l = lmin; l <= L; ++l) {
     Level& lv = S.lev[l];
     if (!lv.ntiles) continue;
-    const Level fine = l < L ? S.lev[l + 1] : none();
+    const View<T> fine = l < L ? view<T>(S.lev[l + 1]) : none<T>();
     const double gscale = o.variant == ADAFAC_VARIANT_EXP ? std::pow(o.omega_exp, L - l) : 1.0;
-    k_br_correct<D><<<lv.ntiles, kT, 0, s>>>(lv, fine, st, o.variant, o.omega, o.omega_tilde,
-                                            gscale, S.ctl);
+    k_br_correct<D, T><<<lv.ntiles, kT, 0, s>>>(view<T>(lv), fine, st, o.variant, o.omega,
+                                               o.omega_tilde, gscale, S.ctl);
   }
   int lcount = lmin;  // the cycle is counted by the finest level that has cells
   for (int l = lmin; l <= L; ++l)
@@ -828,8 +957,42 @@ void cycle_d(System& S, const adafac_options& o, bool with_norm, cudaStream_t s)
   for (int l = lmin; l <= L; ++l) {
     Level& lv = S.lev[l];
     if (!lv.ntiles) continue;
-    const Level coarse = l > lmin ? S.lev[l - 1] : none();
-    k_br_prolong<D><<<lv.ntiles, kT, 0, s>>>(lv, coarse, S.ctl, l == lcount ? 1 : 0);
+    const View<T> coarse = l > lmin ? view<T>(S.lev[l - 1]) : none<T>();
+    k_br_prolong<D, T><<<lv.ntiles, kT, 0, s>>>(view<T>(lv), coarse, S.ctl, l == lcount ? 1 : 0);
+  }
+}
+
+template <int D>
+void cycle_d(System& S, const adafac_options& o, bool with_norm, cudaStream_t s) {
+  // the norm runs over every level's nodal-space vertices: the chain goes to
+  // level 1 when it is evaluated
+  residual_chain<D, double>(S, with_norm ? 1 : o.lmin, false, with_norm, s);
+  if (with_norm) k_br_finalize<<<1, kT, 0, s>>>(S.part, S.npart, S.ctl, 0);
+  corrections<D, double>(S, o, s);
+}
+
+// The correction equation's cycles see rho^e_l = Phi_l^T (r - K e) as the
+// step's FP64 rho_l rounded to FP32 plus the FP32 chain of the leaf cells'
+// -K e.  The FP64 rho_l tends to zero at the active vertices as the solve
+// converges; the composite residual r itself does not (at hanging nodes,
+// which carry no unknown, it stays of the load's size), so rounding r or
+// the levels' parts of it to FP32 would stall the solve near FP32 epsilon.
+template <int D>
+void step_d(System& S, const adafac_options& o, int k, bool with_norm, cudaStream_t s) {
+  residual_chain<D, double>(S, 1, false, true, s);
+  if (with_norm) k_br_finalize<<<1, kT, 0, s>>>(S.part, S.npart, S.ctl, 0);
+  for (int l = 1; l <= S.L; ++l) {
+    Level& lv = S.lev[l];
+    if (lv.ntiles) k_br_round<D><<<lv.ntiles, kT, 0, s>>>(lv.n, lv.tiles, lv.R, lv.RHS32, S.ctl);
+  }
+  for (int j = 0; j < k; ++j) {
+    residual_chain<D, float>(S, o.lmin, false, false, s);
+    corrections<D, float>(S, o, s);
+  }
+  for (int l = o.lmin; l <= S.L; ++l) {
+    Level& lv = S.lev[l];
+    if (!lv.ntiles) continue;
+    k_br_add_correction<D><<<lv.ntiles, kT, 0, s>>>(lv.n, lv.tiles, lv.U, lv.E32, S.ctl);
   }
 }
 
@@ -840,9 +1003,14 @@ void enqueue_cycle(System& S, const adafac_options& o, bool with_norm, cudaStrea
   else cycle_d<3>(S, o, with_norm, s);
 }
 
+void enqueue_step(System& S, const adafac_options& o, int k, bool with_norm, cudaStream_t s) {
+  if (S.D == 2) step_d<2>(S, o, k, with_norm, s);
+  else step_d<3>(S, o, k, with_norm, s);
+}
+
 void enqueue_norm(System& S, cudaStream_t s) {
-  if (S.D == 2) residual_chain<2>(S, 1, true, s);
-  else residual_chain<3>(S, 1, true, s);
+  if (S.D == 2) residual_chain<2, double>(S, 1, true, true, s);
+  else residual_chain<3, double>(S, 1, true, true, s);
   k_br_finalize<<<1, kT, 0, s>>>(S.part, S.npart, S.ctl, 1);
 }
 
@@ -891,7 +1059,7 @@ void from_node_values(System& S, const int* node_map, const double* v, cudaStrea
     if (!lv.ntiles) continue;
     Level cur = lv;
     if (!cur.T) cur.T = cur.G;  // the finest level keeps its chain value in G (scratch)
-    const Level coarse = l > 1 ? S.lev[l - 1] : none();
+    const Level coarse = l > 1 ? S.lev[l - 1] : Level();
     if (S.D == 2)
       k_br_from_values<2><<<lv.ntiles, kT, 0, s>>>(cur, coarse, S.L, N1, node_map, v);
     else

@@ -55,13 +55,18 @@ struct Level {
   double *EL = nullptr;              // eps of the level's leaf cells, else 0
   uint8_t *nodal = nullptr;          // the position's finest active level is l
   uint8_t *leaf = nullptr;           // leaf cells
-  int* tiles = nullptr;              // tiles meeting an existing cell
+  // mixed solves: the FP32 correction E_l, its chains, and the FP32 copies
+  // of 1 / M_l, eps and of the step's FP64 rho_l (RHS32)
+  float *E32 = nullptr, *R32 = nullptr, *G32 = nullptr, *T32 = nullptr;
+  float *IM32 = nullptr, *EL32 = nullptr, *RHS32 = nullptr;
+  int2* tiles = nullptr;             // tiles meeting an existing cell (column | row << 16, plane)
   int ntiles = 0;
   int part_off = 0;                  // first norm partial of the level
 };
 
 struct System {
   int D = 0, L = 0;
+  bool mixed = false;                // FP32 cycles with FP64 refinement steps
   Level lev[kMaxL + 1];
   double* part = nullptr;            // one norm partial per tile of every level
   int npart = 0;
@@ -78,13 +83,17 @@ struct Tree {
 // Builds the system on the device: eps (scalar or per fine cell) and f (at
 // the fine positions) are host arrays.  Synchronises the stream.
 adafac_status build(System& S, int D, int L, const Tree& tree, const double* eps, int eps_scalar,
-                    const double* f, cudaStream_t s, std::string* err);
+                    const double* f, bool mixed, cudaStream_t s, std::string* err);
 void release(System& S);
 // One cycle (Eq. 9 on the generating system) of the given variant over
 // levels lmin .. L.  with_norm: its residual norm is evaluated first, and
 // once rel <= ctl->tol (a solve) the cycle and the rest of the batch return
 // at entry.
 void enqueue_cycle(System& S, const adafac_options& o, bool with_norm, cudaStream_t s);
+// Mixed solves: one refinement step -- the FP64 level residuals rho_l (their
+// norm first when with_norm), rounded to FP32, k FP32 cycles on the
+// correction equation, U_l += E_l.
+void enqueue_step(System& S, const adafac_options& o, int k, bool with_norm, cudaStream_t s);
 // The residual chain of every level and the norm of Eq. 10 into ctl->abs / rel.
 void enqueue_norm(System& S, cudaStream_t s);
 // Leaf-node vectors (fine-grid indices nodes[0 .. nn)) <-> the level copies.

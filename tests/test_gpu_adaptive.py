@@ -248,3 +248,55 @@ def test_brick_and_csr_engines_give_the_same_iterates(tree, d, L, variant):
     for l in range(L):
         _close(out["auto"][2][l], out["generic"][2][l], f"g_{l + 1}", 1e-12,
                scale=np.abs(out["generic"][2][l]).max() + 1e-300)
+
+
+FP32_RTOL = 5e-5
+
+
+@pytest.mark.parametrize("tree,d,L", [("band", 2, 4), ("corner", 2, 4), ("band", 3, 3)])
+@pytest.mark.parametrize("variant", ["jac", "additive", "pi"])
+@pytest.mark.parametrize("k", [1, 3])
+def test_mixed_refinement_step_matches_the_oracle(tree, d, L, variant, k):
+    # one refinement step of k FP32 cycles on the correction equation equals
+    # k FP64 oracle cycles (the cycle is linear in the residual) up to FP32
+    # rounding: 5e-5 of the correction's largest entry (the bound of the
+    # regular path's mixed tests: 6e-8 per operation, eps ratios to 15,
+    # k <= 3 cycles over several levels)
+    T, eps, f, S = _problem(tree, d, L)
+    u0 = _start(S)
+    u = u0
+    for _ in range(k):
+        u = ad.cycle(S, u, variant=variant)
+    o = adafac.default_options(precision="mixed", variant=variant, inner_cycles=k)
+    G = adafac.AdaptiveSolver(T.d, T.L, [T.refined[l] for l in range(1, T.L)], eps, f, o)
+    G.set_solution(u0)
+    G.cycle(k)
+    got = G.solution() - u0
+    G.close()
+    _close(got, u - u0, "mixed step correction", FP32_RTOL)
+
+
+@pytest.mark.parametrize("tree,d,L", [("band", 2, 4), ("corner", 3, 3)])
+def test_mixed_solve_meets_the_oracle_residual(tree, d, L):
+    T, eps, f, S = _problem(tree, d, L)
+    o = adafac.default_options(precision="mixed")
+    G = adafac.AdaptiveSolver(T.d, T.L, [T.refined[l] for l in range(1, T.L)], eps, f, o)
+    cycles, rel = G.solve(1e-8, 5000)
+    assert rel <= 1e-8
+    ug = G.solution()
+    r0 = ad.residual_norm(S, np.zeros(len(S.coords)))
+    assert ad.residual_norm(S, ug) / r0 <= 1.01e-8
+    # the FP64 engine needs the same cycles, up to one refinement step
+    G64 = _gpu(T, eps, f)
+    c64, _ = G64.solve(1e-8, 5000)
+    assert abs(c64 - cycles) <= o.inner_cycles
+    G.close()
+    G64.close()
+
+
+def test_mixed_is_refused_on_the_sparse_matrix_engine():
+    T, eps, f, S = _problem("band", 2, 3)
+    for opt in (dict(path="generic"), dict(rtilde="exact")):
+        o = adafac.default_options(precision="mixed", **opt)
+        with pytest.raises(adafac.AdafacError):
+            adafac.AdaptiveSolver(T.d, T.L, [T.refined[l] for l in range(1, T.L)], eps, f, o)
