@@ -296,6 +296,54 @@ __global__ void __launch_bounds__(kT)
   lv.U[v] += t;
 }
 
+// The finest level in one pass: g_L = gscale c_L (nothing above it damps
+// it), T_L = g_L + P T_{L-1}, U_L += T_L.  g_L is kept for inspection.
+template <int D, typename T>
+__global__ void __launch_bounds__(kT)
+    k_br_finest(const View<T> lv, const View<T> coarse, double omega, double gscale, Ctl* ctl,
+                int count) {
+  if (halted(ctl)) return;
+  if (count && blockIdx.x == 0 && threadIdx.x == 0) ctl->applied += 1;
+  int c[3];
+  if (!tile_vertex<D>(lv.n, lv.tiles[blockIdx.x], c)) return;
+  const int n = lv.n, np1 = n + 1;
+  const long long v = vidx<D>(c, np1);
+  const T im = lv.IM[v];
+  const T g = im > T(0) ? T(gscale) * (T(omega) * (lv.R[v] + (lv.R0 ? lv.R0[v] : T(0))) * im) : T(0);
+  lv.G[v] = g;
+  if (!inner<D>(c, n)) return;
+  T t = g;
+  if (coarse.n) {
+    const int nc = coarse.n, ncp1 = nc + 1;
+    int O[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      O[j] = min(c[j] / 3, nc - 1);
+      lo[j] = c[j] - 3 * O[j];
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int e = 0; e < (1 << D); ++e) {
+      bool zero = false;
+      T w = T(1);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int bit = (e >> j) & 1;
+        zero = zero || (bit && lo[j] == 0);
+        const T tt = lo[j] == 0 ? T(0) : (lo[j] == 1 ? T(1.0 / 3.0) : T(2.0 / 3.0));
+        w *= bit ? tt : T(1) - tt;
+      }
+      if (zero) continue;
+      const int ex = e & 1, ey = (e >> 1) & 1, ez = (e >> 2) & 1;
+      const long long cv = D == 2 ? (long long)(O[1] + ey) * ncp1 + O[0] + ex
+                                  : ((long long)(O[2] + ez) * ncp1 + O[1] + ey) * ncp1 + O[0] + ex;
+      acc += w * coarse.Tc[cv];
+    }
+    t += acc;
+  }
+  lv.U[v] += t;
+}
+
 // mixed solve: the step's FP64 rho_l rounded to FP32, over the level's tiles
 template <int D>
 __global__ void __launch_bounds__(kT)
@@ -943,10 +991,12 @@ void corrections(System& S, const adafac_options& o, cudaStream_t s) {
   const int L = S.L, lmin = o.lmin;
   Stencil5<T> st;
   for (int k = 0; k < 125; ++k) st.w[k] = (T)S.stilde[k];
-  for (int l = lmin; l <= L; ++l) {
+  // levels below the finest: corrections, then the prolongation chain; the
+  // finest level's correction and update in one pass after them
+  for (int l = lmin; l < L; ++l) {
     Level& lv = S.lev[l];
     if (!lv.ntiles) continue;
-    const View<T> fine = l < L ? view<T>(S.lev[l + 1]) : none<T>();
+    const View<T> fine = view<T>(S.lev[l + 1]);
     const double gscale = o.variant == ADAFAC_VARIANT_EXP ? std::pow(o.omega_exp, L - l) : 1.0;
     k_br_correct<D, T><<<lv.ntiles, kT, 0, s>>>(view<T>(lv), fine, st, o.variant, o.omega,
                                                o.omega_tilde, gscale, S.ctl);
@@ -954,11 +1004,16 @@ void corrections(System& S, const adafac_options& o, cudaStream_t s) {
   int lcount = lmin;  // the cycle is counted by the finest level that has cells
   for (int l = lmin; l <= L; ++l)
     if (S.lev[l].ntiles) lcount = l;
-  for (int l = lmin; l <= L; ++l) {
+  for (int l = lmin; l < L; ++l) {
     Level& lv = S.lev[l];
     if (!lv.ntiles) continue;
     const View<T> coarse = l > lmin ? view<T>(S.lev[l - 1]) : none<T>();
     k_br_prolong<D, T><<<lv.ntiles, kT, 0, s>>>(view<T>(lv), coarse, S.ctl, l == lcount ? 1 : 0);
+  }
+  if (S.lev[L].ntiles) {
+    const View<T> coarse = L > lmin ? view<T>(S.lev[L - 1]) : none<T>();
+    k_br_finest<D, T><<<S.lev[L].ntiles, kT, 0, s>>>(view<T>(S.lev[L]), coarse, o.omega, 1.0,
+                                                    S.ctl, L == lcount ? 1 : 0);
   }
 }
 
