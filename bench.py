@@ -271,7 +271,7 @@ def _tuning_summary(t):
     if not t:
         return None
     if t["path"] == 1:
-        shapes = {"sweep_zc": t["sweep_zc"], "sweep_zc_down": t["sweep_zc_down"]}
+        shapes = {"sweep_nz": t["sweep_nz"], "sweep_nz_down": t["sweep_nz_down"]}
     elif t["path"] == 2:
         shapes = {k: t[k] for k in ("res_bx", "res_by", "res_zr", "upd_bx", "upd_by")}
     else:

@@ -310,9 +310,10 @@ adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
  * the fastest (a candidate replaces the default only when it is at least 2 %
  * faster):
  *   path 1, the fused 3-D sweeps (MIXED, scalar eps, d-linear, 3-D): the
- *     depth of the up-pass and down-pass tiles in coarse planes per block
- *     (sweep_zc, sweep_zc_down: every distinct ceil((3^(L-1)+1) / chunks)
- *     from 3 to 24);
+ *     number of balanced slabs along z into which the up-passes split the
+ *     interior coarse planes and the down-passes the interior fine planes
+ *     (sweep_nz, sweep_nz_down: every count whose slabs are 3 to 24 coarse
+ *     planes thick);
  *   path 2, the grid-shaped level kernels (MIXED otherwise, path not
  *     GENERIC): the block shape of the fine residual and of the fine update
  *     (res_bx x res_by, upd_bx x upd_by threads from 32x8, 64x4, 32x4,
@@ -332,8 +333,8 @@ adafac_status adafac_timing_read(adafac_handle h, int kind, double* total_ms,
 typedef struct {
   int path;            /* 0 nothing tuned, 1 fused 3-D sweeps, 2 level kernels */
   int cached;          /* 1: taken from an earlier tuning of the same shape   */
-  int sweep_zc;        /* path 1: coarse planes per block of the up-passes    */
-  int sweep_zc_down;   /* path 1: coarse planes per block of the down-passes  */
+  int sweep_nz;        /* path 1: slabs along z of the up-passes              */
+  int sweep_nz_down;   /* path 1: slabs along z of the down-passes            */
   int res_bx, res_by;  /* path 2: threads per block of the fine residual      */
   int res_zr;          /* path 2: planes per thread column (0 = size rule)    */
   int upd_bx, upd_by;  /* path 2: threads per block of the fine update        */

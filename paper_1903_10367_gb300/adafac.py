@@ -54,8 +54,8 @@ REQUEST_STATE = {0: "pending", 1: "running", 2: "done", 3: "failed"}
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("path", ctypes.c_int), ("cached", ctypes.c_int), ("sweep_zc", ctypes.c_int),
-                ("sweep_zc_down", ctypes.c_int), ("res_bx", ctypes.c_int),
+    _fields_ = [("path", ctypes.c_int), ("cached", ctypes.c_int), ("sweep_nz", ctypes.c_int),
+                ("sweep_nz_down", ctypes.c_int), ("res_bx", ctypes.c_int),
                 ("res_by", ctypes.c_int), ("res_zr", ctypes.c_int), ("upd_bx", ctypes.c_int),
                 ("upd_by", ctypes.c_int), ("candidates", ctypes.c_int),
                 ("us_default", ctypes.c_double), ("us_tuned", ctypes.c_double)]

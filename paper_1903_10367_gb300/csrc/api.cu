@@ -482,17 +482,12 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
     sw.n = fine.n;
     sw.nc = h->lev[L - 1].n;
     {
-      // coarse planes per block: about one wave of blocks at three per SM
+      // slabs along z: as many as one wave of resident blocks allows
       int dev = 0, nsm = 152;
       if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      const int ncp1 = h->lev[L - 1].n + 1;
-      const int tiles = ((ncp1 + kUpBJX - 1) / kUpBJX) * ((ncp1 + kUpBJY - 1) / kUpBJY);
-      const int chunks = std::max(1, (3 * nsm) / tiles);
-      sw.zc = std::max(3, (ncp1 + chunks - 1) / chunks);
-      const int tiles_d = ((3 * (ncp1 - 1) + 63) / 64) * ((ncp1 + kSweepBJY - 1) / kSweepBJY);
-      const int chunks_d = std::max(1, (3 * nsm) / tiles_d);
-      sw.zc_down = std::max(3, (ncp1 + chunks_d - 1) / chunks_d);
+      sw.nz = sweep3_default_nz(sw.nc, nsm);
+      sw.nz_down = sweep3_default_nz_down(sw.nc, nsm);
     }
     sw.a_c = (float)a.cst[13];
     sw.a_f = (float)a.cst[12];
@@ -1131,14 +1126,14 @@ double time_us(adafac_handle h, int reps, F&& launch) {
   return 1e3 * ms / reps;
 }
 
-// Coarse planes per block of the fused sweeps worth timing: every distinct
-// ceil(ncp1 / chunks) from 3 up to 24.
-std::vector<int> zc_candidates(int ncp1) {
+// Slab counts along z of the fused sweeps worth timing: every count whose
+// slabs are 3 to 24 coarse planes thick (planes: the interior planes of the
+// sweep's level, 3 per coarse plane on the fine level), at least one.
+std::vector<int> nz_candidates(int planes, int per_coarse) {
+  const int lo = std::max(1, (planes + 24 * per_coarse - 1) / (24 * per_coarse));
+  const int hi = std::max(lo, planes / (3 * per_coarse));
   std::vector<int> out;
-  for (int chunks = 1; chunks <= ncp1; ++chunks) {
-    const int zc = std::max(3, (ncp1 + chunks - 1) / chunks);
-    if (zc <= 24 && std::find(out.begin(), out.end(), zc) == out.end()) out.push_back(zc);
-  }
+  for (int nz = lo; nz <= hi; ++nz) out.push_back(nz);
   return out;
 }
 
@@ -1210,30 +1205,34 @@ adafac_status tune_fast3(adafac_handle h, int reps, adafac_tuning* t) {
   Sweep3Params p = h->sw;
   p.q = L - 1 == lmin ? h->lev[lmin].g32 : h->lev[L - 1].t32;
   p.e_out = h->e32b;
-  auto sweep = [&](int mode, int zc) {
+  auto sweep = [&](int mode, int nz) {
     Sweep3Params q = p;
-    if (mode == SWEEP_UPE) q.zc = zc;
-    else q.zc_down = zc;
+    if (mode == SWEEP_UPE) q.nz = nz;
+    else q.nz_down = nz;
     return time_us(h, reps, [&] { launch_sweep3(q, h->maps, mode == SWEEP_UPE ? 1 : 0, mode, s); });
   };
-  const int ncp1 = h->lev[L - 1].n + 1;
-  const double up0 = sweep(SWEEP_UPE, p.zc), down0 = sweep(SWEEP_DOWN, p.zc_down);
+  const int nc = h->lev[L - 1].n;
+  const double up0 = sweep(SWEEP_UPE, p.nz), down0 = sweep(SWEEP_DOWN, p.nz_down);
   if (up0 < 0.0 || down0 < 0.0) return check_cuda(h, "autotune timing");
   double best_up = up0, best_down = down0;
-  int zc = p.zc, zcd = p.zc_down, timed = 2;
-  for (int c : zc_candidates(ncp1)) {
-    const double u = sweep(SWEEP_UPE, c), d = sweep(SWEEP_DOWN, c);
-    timed += 2;
-    if (u > 0.0 && u < best_up) best_up = u, zc = c;
-    if (d > 0.0 && d < best_down) best_down = d, zcd = c;
+  int nz = p.nz, nzd = p.nz_down, timed = 2;
+  for (int c : nz_candidates(nc - 1, 1)) {
+    const double u = sweep(SWEEP_UPE, c);
+    timed += 1;
+    if (u > 0.0 && u < best_up) best_up = u, nz = c;
   }
-  if (best_up > 0.98 * up0) zc = p.zc, best_up = up0;
-  if (best_down > 0.98 * down0) zcd = p.zc_down, best_down = down0;
-  h->sw.zc = zc;
-  h->sw.zc_down = zcd;
+  for (int c : nz_candidates(3 * nc - 1, 3)) {
+    const double d = sweep(SWEEP_DOWN, c);
+    timed += 1;
+    if (d > 0.0 && d < best_down) best_down = d, nzd = c;
+  }
+  if (best_up > 0.98 * up0) nz = p.nz, best_up = up0;
+  if (best_down > 0.98 * down0) nzd = p.nz_down, best_down = down0;
+  h->sw.nz = nz;
+  h->sw.nz_down = nzd;
   t->path = 1;
-  t->sweep_zc = zc;
-  t->sweep_zc_down = zcd;
+  t->sweep_nz = nz;
+  t->sweep_nz_down = nzd;
   t->candidates = timed;
   t->us_default = up0 + down0;
   t->us_tuned = best_up + best_down;
@@ -1242,8 +1241,8 @@ adafac_status tune_fast3(adafac_handle h, int reps, adafac_tuning* t) {
 
 void apply_tuning(adafac_handle h, const adafac_tuning& t) {
   if (t.path == 1) {
-    h->sw.zc = t.sweep_zc;
-    h->sw.zc_down = t.sweep_zc_down;
+    h->sw.nz = t.sweep_nz;
+    h->sw.nz_down = t.sweep_nz_down;
   } else if (t.path == 2) {
     h->res_shape.bx = t.res_bx;
     h->res_shape.by = t.res_by;

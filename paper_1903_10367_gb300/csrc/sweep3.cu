@@ -46,18 +46,20 @@ namespace {
 
 // down-pass tiles: 64 fine columns x OH rows; the coarse window of the
 // prolongation is QW x QH coarse columns
-constexpr int BJY = kSweepBJY;
-constexpr int OH = 3 * BJY;                 // owned fine rows per block: 24
+constexpr int OH = kDownRows;               // owned fine rows per block: 22
 constexpr int NPAIR = 32;                   // thread column pairs
-constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane: 68 x 30
-constexpr int PLANE_F = 2048;               // floats per staged plane (128-byte multiple)
+constexpr int BOXW = kBoxW, BOXH = kBoxH;   // staged box of a plane: 68 x 24
+constexpr int PLANE_F = 1632;               // floats per staged plane (128-byte multiple)
 constexpr int NSTAGE = 3, PREF = 2;         // ring slots, planes staged ahead
-constexpr int QW = 24, QH = BJY + 4;        // coarse q window
+// the rows y0 .. y0 + OH - 1 interpolate between the coarse rows floor(y0 / 3)
+// .. floor((y0 + OH - 1) / 3) + 1: at most (OH + 1) / 3 + 2 of them
+constexpr int QW = 24, QH = 10;             // coarse q window
 constexpr int NQX = QH * 64;                // x-interpolated coarse values per plane
+static_assert(QH >= (OH + 1) / 3 + 2, "the q window covers the rows' coarse rows");
 
-static_assert(BOXW * BOXH <= PLANE_F, "staged box fits its slot");
+static_assert(BOXW * BOXH <= PLANE_F && (PLANE_F * 4) % 128 == 0, "staged box fits its slot");
 static_assert((BOXW * 4) % 16 == 0, "box rows are 16-byte multiples");
-static_assert(BOXW >= 68 && BOXH >= OH + 6, "the box covers 64 columns and the rows + halo");
+static_assert(BOXW >= 68 && BOXH >= OH + 2, "the box covers 64 columns and the rows + halo");
 
 // the slot refilled at step t (that of t + PREF) was last read at step
 // t + PREF - NSTAGE <= t - 1, before the block barrier that opens step t
@@ -121,7 +123,8 @@ __device__ __forceinline__ Parts parts(const RowPair& up, const RowPair& ce, con
 
 // ---- down-passes ----------------------------------------------------------------
 // A block owns 64 fine columns in x (all 32 lane pairs busy; no coarse
-// alignment is needed), OH rows and zc_down coarse planes.  NT threads are 32
+// alignment is needed), OH rows and one of gridDim.z balanced slabs of the
+// interior planes 1 .. n - 1 (no coarse alignment is needed in z either).  NT threads are 32
 // column pairs x NT/32 row strips; MINB blocks per SM.
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
@@ -129,8 +132,9 @@ __global__ void __launch_bounds__(NT, MINB)
             const __grid_constant__ CUtensorMap tm_rhs) {
   static_assert(MODE == SWEEP_DOWN || MODE == SWEEP_DOWNU, "down-pass modes");
   constexpr int NSTRIP = NT / NPAIR;
-  constexpr int RB = OH / NSTRIP;                        // rows per strip
-  static_assert(OH % NSTRIP == 0 && NQX % NT == 0, "thread tiling");
+  constexpr int RBB = OH / NSTRIP, RBX = OH % NSTRIP;
+  constexpr int RB = RBB + (RBX ? 1 : 0);                // rows of the longest strip
+  static_assert(NQX % NT == 0, "thread tiling");
   extern __shared__ __align__(128) float smem[];
   __shared__ int s_fail;
   if (halted(p.ctl)) return;
@@ -145,11 +149,10 @@ __global__ void __launch_bounds__(NT, MINB)
   const long long fplane = (long long)ldx * (n + 1);
   const int tid = threadIdx.x;
   const int pc = tid % NPAIR, strip = tid / NPAIR;
-  const int Jy0 = blockIdx.y * BJY;
-  const int Jz0 = blockIdx.z * p.zc_down;
-  const int Jz1 = min(Jz0 + p.zc_down, ncp1);
-  const int xA = 64 * (int)blockIdx.x - 4, yA = 3 * Jy0 - 4;  // staged box origin
-  const int oz0 = 3 * Jz0 - 1, oz1 = 3 * Jz1 - 1;          // owned planes [oz0, oz1)
+  const int Y0 = 1 + blockIdx.y * OH;                     // first owned row
+  const int xA = 64 * (int)blockIdx.x - 4, yA = Y0 - 1;     // staged box origin
+  const int oz0 = 1 + (int)((long long)blockIdx.z * (n - 1) / gridDim.z);  // owned planes
+  const int oz1 = 1 + (int)((long long)(blockIdx.z + 1) * (n - 1) / gridDim.z);  // [oz0, oz1)
   // step t stages e plane t and rhs plane t-1 and updates plane s = t-1
   // (W + Y of planes s-1 .. s+1 are known at step t)
   const int t0 = oz0 - 1, t1 = oz1 + 1;
@@ -172,24 +175,27 @@ __global__ void __launch_bounds__(NT, MINB)
     for (int t = t0; t < t0 + PREF && t < t1; ++t) issue(t);
 
   // the pair (2 pc, 2 pc + 1) of the owned box is box columns 3 + 2 pc (+1);
-  // row strip RB + i is box row 3 + strip RB + i
+  // the strip's owned rows rs0 + i (i < nr) are box rows rs0 + i + 1
+  const int rs0 = strip * RBB + min(strip, RBX);
+  const int nr = RBB + (strip < RBX ? 1 : 0);
   const int xb = xA + 3 + 2 * pc;                          // odd
   const float2 mxB = make_float2(xb >= 1 && xb <= n - 1 ? 1.f : 0.f,
                                  xb + 1 >= 1 && xb + 1 <= n - 1 ? 1.f : 0.f);
-  const int y0 = yA + 3 + strip * RB;
+  const int y0 = Y0 + rs0;
+  const int qy0 = min(Y0 / 3, nc - 1);                     // first coarse row of the window
   float myB[RB];
   int qrB[RB];
   float tyB[RB];
 #pragma unroll
   for (int i = 0; i < RB; ++i) {
     const int y = y0 + i;
-    myB[i] = y >= 1 && y <= n - 1 ? 1.f : 0.f;
+    myB[i] = i < nr && y >= 1 && y <= n - 1 ? 1.f : 0.f;
     const int Oy = min(max(y, 0) / 3, nc - 1);
-    qrB[i] = (Oy - (Jy0 - 2)) * 64 + 2 * pc;
+    qrB[i] = i < nr ? (Oy - qy0) * 64 + 2 * pc : 0;
     tyB[i] = (float)(y - 3 * Oy) * (1.f / 3.f);
   }
   // prolongation of q: per plane the z-interpolated coarse window sQ (QW x QH,
-  // origin (qx0, J0y - 2)), then the x-interpolated values sQX at the owned
+  // origin (qx0, qy0)), then the x-interpolated values sQX at the owned
   // columns; each thread interpolates in y itself.  The owned columns x in
   // [xA + 3, xA + 67) interpolate between coarse columns floor(x / 3) and + 1.
   constexpr int NQ = (QW * QH + NT - 1) / NT, NX = NQX / NT;
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     const int e = tid + k * NT;
-    const int Jx = qx0 + e % QW, Jy = Jy0 - 2 + e / QW;
+    const int Jx = qx0 + e % QW, Jy = qy0 + e / QW;
     qok[k] = e < QW * QH && Jx >= 0 && Jx <= nc && Jy >= 0 && Jy <= nc;
     qoff[k] = qok[k] ? Jy * ncp1 + Jx : 0;
   }
@@ -291,8 +297,8 @@ __global__ void __launch_bounds__(NT, MINB)
     const float* sRhs = sE + PLANE_F;
     const int s = t - 1;
     const bool doB = s >= oz0 && s < oz1 && s >= 1 && s <= n - 1;
-    const float* E = sE + (strip * RB + 2) * BOXW + 2 + 2 * pc;
-    const float* Rh = sRhs + (strip * RB + 3) * BOXW + 3 + 2 * pc;
+    const float* E = sE + rs0 * BOXW + 2 + 2 * pc;
+    const float* Rh = sRhs + (rs0 + 1) * BOXW + 3 + 2 * pc;
     const float* qx = sQX + (s & 1) * NQX;
     // DOWNU: fetch the FP64 iterate first (its latency overlaps the stencil)
     double uo[RB][2];
@@ -307,6 +313,7 @@ __global__ void __launch_bounds__(NT, MINB)
     RowPair up = row_pair(E), ce = row_pair(E + BOXW);
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
+      if (i >= nr) break;
       const RowPair dn = row_pair(E + (i + 2) * BOXW);
       const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
       if (doB && myB[i] != 0.f) {
@@ -367,31 +374,41 @@ __global__ void __launch_bounds__(NT, MINB)
 }
 
 // ---- up-passes on wide tiles -------------------------------------------------
-// A block owns UBJX x UBJY coarse columns (41 x 4: two x-tiles cover the 82
-// coarse columns of a 243-cell grid exactly) and zc coarse planes.  Its 256
-// threads are 64 column pairs (two warps per row) x 4 row strips.  The
-// residual region is the owned fine box + 1 (125 x 14 fine columns), computed
-// by 63 pairs whose first column is odd, starting at cstart = 3 J0x - 2 (J0x
-// odd) or 3 J0x - 3 (J0x even); the staged box starts at the 16-byte boundary
-// at or below cstart - 1 and is 132 x 16 floats.
+// A block owns UBJX x UBJY interior coarse columns (20 x 8, from column and row
+// 1: four x-tiles and ten y-tiles cover the 80 x 80 interior coarse columns of
+// a 243-cell grid exactly, and the 160 restriction targets are five full
+// warps) and one of gridDim.z balanced slabs of the interior coarse planes
+// 1 .. nc - 1.  Its 256 threads are 32 column pairs (one warp per row) x 8 row
+// strips.  The residual region is the owned fine box + 1 (62 x 26 fine
+// columns), computed by the first UNACT pairs, whose first column is odd,
+// starting at cstart = 3 J0x - 2 (J0x odd) or 3 J0x - 3 (J0x even); the staged
+// box starts at the 16-byte boundary at or below cstart - 1 and is 64 x 28
+// floats.  Strips 0 and 1 take 4 residual rows, the others 3; warps 2 .. 6
+// also restrict.
 constexpr int UBJX = kUpBJX, UBJY = kUpBJY;
-constexpr int UNT = 256, UNPAIR = 64, UNSTRIP = UNT / UNPAIR;
+constexpr int UNT = 256, UNPAIR = 32, UNSTRIP = UNT / UNPAIR;
+constexpr int kUpMinB = 3;                              // blocks per SM
+constexpr int UNACT = (3 * UBJX + 3) / 2;               // pairs of the residual region (31)
 constexpr int UBOXW = kUpBoxW, UBOXH = kUpBoxH;
-constexpr int UPLANE_F = UBOXW * UBOXH;                 // 2112 floats: 128-byte multiple
-constexpr int UCH = 3 * UBJY + 2;                       // residual rows (14)
+constexpr int UPLANE_F = UBOXW * UBOXH;                 // 1792 floats: 128-byte multiple
+constexpr int UCH = 3 * UBJY + 2;                       // residual rows (26)
 constexpr int URCB = UCH / UNSTRIP, URCX = UCH % UNSTRIP;
 constexpr int URC = URCB + (URCX ? 1 : 0);
-constexpr int USR_P = 130;                              // residual-plane pitch
+// residual-plane pitch: 84 = 20 mod 32 keeps the restriction's loads free of
+// bank conflicts (a warp's targets span up to three coarse rows)
+constexpr int USR_P = 84;
 constexpr int USR_F = USR_P * UCH;
-constexpr int UNJ = UBJX * UBJY;                        // 164 coarse columns
+constexpr int UNJ = UBJX * UBJY;                        // 160 coarse columns
+constexpr int UJ0 = URCX * UNPAIR;                      // first restricting thread
 constexpr int UOFF_SR = NSTAGE * 2 * UPLANE_F;
 constexpr int UOFF_BAR = UOFF_SR + 2 * USR_F;
 constexpr size_t USMEM_BYTES = (size_t)UOFF_BAR * 4 + NSTAGE * 8 + 16;
 static_assert((UPLANE_F * 4) % 128 == 0 && UOFF_SR % 2 == 0 && UOFF_BAR % 2 == 0, "alignment");
-static_assert(UNJ <= UNT && 2 * (UNPAIR - 1) >= 3 * UBJX + 3, "thread counts");
+static_assert(UJ0 + UNJ <= UNT && UNACT <= UNPAIR && 2 * UNACT >= 3 * UBJX + 2, "thread counts");
+static_assert(2 * UNACT <= USR_P && UBOXW >= 2 * UNACT + 2, "the residual region fits its planes");
 
 template <int MODE>
-__global__ void __launch_bounds__(UNT, 3)
+__global__ void __launch_bounds__(UNT, kUpMinB)
     k_up3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
           const __grid_constant__ CUtensorMap tm_rhs) {
   static_assert(MODE == SWEEP_UP || MODE == SWEEP_UPE, "up-pass modes");
@@ -409,15 +426,14 @@ __global__ void __launch_bounds__(UNT, 3)
   const int n = p.n, nc = p.nc, ncp1 = nc + 1;
   const int tid = threadIdx.x;
   const int pc = tid % UNPAIR, strip = tid / UNPAIR;
-  const int Jx0 = blockIdx.x * UBJX, Jy0 = blockIdx.y * UBJY;
-  const int Jz0 = blockIdx.z * p.zc;
-  const int Jz1 = min(Jz0 + p.zc, ncp1);
+  const int Jx0 = 1 + blockIdx.x * UBJX, Jy0 = 1 + blockIdx.y * UBJY;
+  const int Jz0 = 1 + (int)((long long)blockIdx.z * (nc - 1) / gridDim.z);  // coarse planes
+  const int Jz1 = 1 + (int)((long long)(blockIdx.z + 1) * (nc - 1) / gridDim.z);  // [Jz0, Jz1)
   const int soff = (Jx0 & 1) ? 0 : 1;                   // restriction column offset in sR
   const int cstart = 3 * Jx0 - 2 - soff;                // odd
   const int xA = ((cstart - 1) >> 2) << 2;              // floor to a multiple of 4
   const int yA = 3 * Jy0 - 3;                           // box row i + 1 = residual row i
-  const int oz0 = 3 * Jz0 - 1, oz1 = 3 * Jz1 - 1;
-  const int zC0 = oz0 - 1, zC1 = oz1 + 1;
+  const int zC0 = 3 * Jz0 - 2, zC1 = 3 * Jz1;          // residual planes [zC0, zC1)
   constexpr bool UPE = MODE == SWEEP_UPE;
   const int t0 = UPE ? zC0 - 1 : zC0, t1 = UPE ? zC1 + 1 : zC1;
   constexpr uint32_t kBytes = (UPE ? 2 : 1) * UBOXW * UBOXH * 4;
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(UNT, 3)
 
   // residual geometry: pair pc = columns c, c + 1 (c = cstart + 2 pc, odd);
   // the last pair has no columns
-  const bool active = pc < UNPAIR - 1;
+  const bool active = pc < UNACT;
   const int c = cstart + 2 * pc;
   const float2 mxC = make_float2(active && c >= 1 && c <= n - 1 ? 1.f : 0.f,
                                  active && c + 1 >= 1 && c + 1 <= n - 1 ? 1.f : 0.f);
@@ -471,9 +487,10 @@ __global__ void __launch_bounds__(UNT, 3)
     dz1[k] = p.dcls[6 + k];
     dz2[k] = p.dcls[12 + k];
   }
-  // restriction geometry: coarse column tid
-  const bool hasJ = tid < UNJ;
-  const int cjx = tid % UBJX, cjy = tid / UBJX;
+  // restriction geometry: coarse column tid - UJ0 (the strips with fewer rows)
+  const int jt = tid - UJ0;
+  const bool hasJ = jt >= 0 && jt < UNJ;
+  const int cjx = hasJ ? jt % UBJX : 0, cjy = hasJ ? jt / UBJX : 0;
   const int Jx = Jx0 + cjx, Jy = Jy0 + cjy;
   const bool outJ = hasJ && Jx >= 1 && Jx <= nc - 1 && Jy >= 1 && Jy <= nc - 1;
 
@@ -846,17 +863,29 @@ bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Ma
   return true;
 }
 
-void sweep3_grid(int nc, int zc, dim3* grid) {
-  const int ncp1 = nc + 1;
-  *grid = dim3((ncp1 + UBJX - 1) / UBJX, (ncp1 + UBJY - 1) / UBJY, (ncp1 + zc - 1) / zc);
+void sweep3_grid(int nc, int nz, dim3* grid) {
+  const int ni = std::max(1, nc - 1);  // interior coarse columns
+  *grid = dim3((ni + UBJX - 1) / UBJX, (ni + UBJY - 1) / UBJY, std::min(std::max(nz, 1), ni));
 }
 
-void sweep3_grid_down(int nc, int zc, dim3* grid) {
-  const int ncp1 = nc + 1;
-  *grid = dim3((3 * nc + 63) / 64, (ncp1 + BJY - 1) / BJY, (ncp1 + zc - 1) / zc);
+void sweep3_grid_down(int nc, int nz, dim3* grid) {
+  const int ni = std::max(1, 3 * nc - 1);  // interior fine rows and planes
+  *grid = dim3((3 * nc + 63) / 64, (ni + OH - 1) / OH, std::min(std::max(nz, 1), ni));
 }
 // threads and blocks per SM of the down-passes
-constexpr int kDownNT = 128, kDownMinB = 3;
+constexpr int kDownNT = 128, kDownMinB = 4;
+
+int sweep3_default_nz(int nc, int nsm) {
+  dim3 g;
+  sweep3_grid(nc, 1, &g);
+  return std::min(std::max(1, (kUpMinB * nsm) / (int)(g.x * g.y)), std::max(1, nc - 1));
+}
+
+int sweep3_default_nz_down(int nc, int nsm) {
+  dim3 g;
+  sweep3_grid_down(nc, 1, &g);
+  return std::min(std::max(1, (kDownMinB * nsm) / (int)(g.x * g.y)), std::max(1, 3 * nc - 1));
+}
 
 bool sweep3_prepare() {
   return cudaFuncSetAttribute(k_up3<SWEEP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -875,9 +904,9 @@ void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int m
                    cudaStream_t s) {
   dim3 grid;
   if (mode == SWEEP_DOWN || mode == SWEEP_DOWNU)
-    sweep3_grid_down(p.nc, p.zc_down, &grid);
+    sweep3_grid_down(p.nc, p.nz_down, &grid);
   else
-    sweep3_grid(p.nc, p.zc, &grid);
+    sweep3_grid(p.nc, p.nz, &grid);
   switch (mode) {
     case SWEEP_UP:
       k_up3<SWEEP_UP><<<grid, UNT, USMEM_BYTES, s>>>(p, maps.e_up[ein], maps.rhs_up);

@@ -12,17 +12,19 @@ namespace adafac {
 // DOWN: down-pass; DOWNU: last down-pass (u += e, the other buffer zeroed)
 enum SweepMode { SWEEP_UP = 0, SWEEP_UPE = 1, SWEEP_DOWN = 2, SWEEP_DOWNU = 3 };
 
-// down-passes: 64 fine columns x 3 kSweepBJY rows per block, staged box
-// 68 x 30 floats (x origin 64 bx - 4, a 16-byte boundary)
-constexpr int kSweepBJY = 8;
-constexpr int kBoxW = 68, kBoxH = 3 * kSweepBJY + 6;
-// up-passes: 41 x 4 coarse columns per block, staged box 132 x 16 floats
-constexpr int kUpBJX = 41, kUpBJY = 4;
-constexpr int kUpBoxW = 132, kUpBoxH = 16;
+// down-passes: 64 fine columns x kDownRows rows per block (tiles from row 1:
+// eleven tiles cover the 242 interior rows of a 243-cell grid exactly), staged
+// box 68 x (kDownRows + 2) floats (x origin 64 bx - 4, a 16-byte boundary)
+constexpr int kDownRows = 22;
+constexpr int kBoxW = 68, kBoxH = kDownRows + 2;
+// up-passes: 20 x 8 interior coarse columns per block, staged box 64 x 28 floats
+constexpr int kUpBJX = 20, kUpBJY = 8;
+constexpr int kUpBoxW = 64, kUpBoxH = 3 * kUpBJY + 4;
 
 struct Sweep3Params {
-  int n = 0, nc = 0, zc = 0;       // fine cells, coarse cells, coarse planes per block
-  int zc_down = 0;                 // coarse planes per block of the down-passes
+  int n = 0, nc = 0;               // fine cells, coarse cells
+  int nz = 1;                      // up-passes: slabs of the interior coarse planes
+  int nz_down = 1;                 // down-passes: slabs of the interior fine planes
   int ldx = 0;                     // row stride of the FP32 fine arrays (multiple of 4)
   // uniform stencil: A e = a_c e + a_f (6 faces) + a_e (12 edges) + a_k (8 corners)
   float a_c = 0, a_f = 0, a_e = 0, a_k = 0;
@@ -78,8 +80,11 @@ bool sweep3_make_maps(float* e0, float* e1, float* rhs, int n, int ldx, Sweep3Ma
 bool sweep3_prepare();
 void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int mode,
                    cudaStream_t s);
-void sweep3_grid(int nc, int zc, dim3* grid);       // up-passes (41 x 4 coarse columns)
-void sweep3_grid_down(int nc, int zc, dim3* grid);  // down-passes (64-column tiles)
+void sweep3_grid(int nc, int nz, dim3* grid);       // up-passes (20 x 8 coarse columns, nz slabs)
+void sweep3_grid_down(int nc, int nz, dim3* grid);  // down-passes (64-column tiles, nz slabs)
+// default slab counts: as many as one wave of resident blocks on nsm SMs allows
+int sweep3_default_nz(int nc, int nsm);
+int sweep3_default_nz_down(int nc, int nsm);
 int refine3_blocks(int n, int zc);
 // planes per block of the refinement residual (one wave of resident blocks)
 int refine3_zc(int n);

@@ -47,15 +47,15 @@ def test_algorithmic_bytes_of_the_level_kernels_count_structural_nonzeros():
 def test_traffic_lookup_checks_sources_and_reports_the_capture_shape():
     w = wl.get("poisson3d_d5")
     good = bench.kernel_source_hash(bench.TRAFFIC_SOURCES["poisson3d_d5"])
-    table = {"poisson3d_d5": {"source_hash": good, "launch_shape": {"sweep_zc": 9, "sweep_zc_down": 9},
+    table = {"poisson3d_d5": {"source_hash": good, "launch_shape": {"sweep_nz": 9, "sweep_nz_down": 9},
                               "bytes": {"fine_up": 123}}}
-    assert bench._traffic_from_profile("fine_up", w, table=table) == (123, {"sweep_zc": 9, "sweep_zc_down": 9})
+    assert bench._traffic_from_profile("fine_up", w, table=table) == (123, {"sweep_nz": 9, "sweep_nz_down": 9})
     assert bench._traffic_from_profile("fine_down", w, table=table)[0] is None
     stale = {"poisson3d_d5": dict(table["poisson3d_d5"], source_hash="0" * 16)}
     assert bench._traffic_from_profile("fine_up", w, table=stale) == (None, None)
-    assert bench._shape_differs({"sweep_zc": 9, "sweep_zc_down": 9}, {"sweep_zc": 8, "sweep_zc_down": 8})
-    assert not bench._shape_differs({"sweep_zc": 9, "sweep_zc_down": 9}, {"sweep_zc": 9, "sweep_zc_down": 9, "path": 1})
-    assert not bench._shape_differs(None, {"sweep_zc": 8})
+    assert bench._shape_differs({"sweep_nz": 9, "sweep_nz_down": 9}, {"sweep_nz": 8, "sweep_nz_down": 8})
+    assert not bench._shape_differs({"sweep_nz": 9, "sweep_nz_down": 9}, {"sweep_nz": 9, "sweep_nz_down": 9, "path": 1})
+    assert not bench._shape_differs(None, {"sweep_nz": 8})
 
 
 def test_committed_traffic_table_matches_the_current_kernel_sources():

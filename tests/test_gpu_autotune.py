@@ -48,7 +48,9 @@ def test_tuned_solve_repeats_the_untuned_one_bit_for_bit(d, L, eps_kind, transfe
     assert rec["candidates"] > 2
     assert 0.0 < rec["us_tuned"] <= rec["us_default"]
     if path == 1:
-        assert 3 <= rec["sweep_zc"] <= 24 and 3 <= rec["sweep_zc_down"] <= 24
+        # slab counts along z: at most one per interior coarse / fine plane
+        assert 1 <= rec["sweep_nz"] <= 3 ** (L - 1) - 1
+        assert 1 <= rec["sweep_nz_down"] <= 3 ** L - 1
     else:
         assert rec["res_bx"] * rec["res_by"] in (128, 256) and rec["res_bx"] % 32 == 0
         assert rec["upd_bx"] * rec["upd_by"] in (128, 256) and rec["upd_bx"] % 32 == 0
@@ -58,7 +60,7 @@ def test_tuned_solve_repeats_the_untuned_one_bit_for_bit(d, L, eps_kind, transfe
     # the same shape again: the stored choice, no timing
     (c2, h2, u2), rec2 = _solve(d, L, eps, f, opts, True)
     assert rec2["cached"] == 1
-    for k in ("path", "sweep_zc", "sweep_zc_down", "res_bx", "res_by", "res_zr", "upd_bx", "upd_by"):
+    for k in ("path", "sweep_nz", "sweep_nz_down", "res_bx", "res_by", "res_zr", "upd_bx", "upd_by"):
         assert rec2[k] == rec[k]
     assert c2 == c0
     np.testing.assert_array_equal(u2, u0)
