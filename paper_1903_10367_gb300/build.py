@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libadafac.so")
 SOURCES = ["setup.cu", "cycle.cu", "level.cu", "sweep3.cu", "coarse3.cu", "api.cu", "noalloc.cu",
            "server.cu", "adaptive.cu", "adaptive_brick.cu", "batch.cu"]
-HEADERS = ["engine.h", "common.cuh", "sweep3.cuh", "mbarrier.cuh", "adaptive_brick.h"]
+HEADERS = ["engine.h", "common.cuh", "sweep3.cuh", "coarse3.cuh", "mbarrier.cuh", "adaptive_brick.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

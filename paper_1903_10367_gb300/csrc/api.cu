@@ -15,6 +15,7 @@
 
 #include "../../include/adafac.h"
 #include "engine.h"
+#include "coarse3.cuh"
 #include "sweep3.cuh"
 
 using namespace adafac;
@@ -814,11 +815,24 @@ void coarse_chain32(adafac_handle h) {
     q.t_f = lv[l].t32;
     return q;
   };
-  for (int l = L - 2; l >= lmin; --l) {
+  // lmin = 1 and level 3 below the finest: levels 2 -> 1 -> 2 -> 3 in one launch
+  Bottom3Params bp;
+  const bool bottom = lmin == 1 && L - 1 >= 3;
+  if (bottom) {
+    bp.r21 = restrict_to(1);
+    bp.p12 = prolong_to(2);
+    bp.p23 = prolong_to(3);
+  }
+  const bool fused = bottom && bottom3u_applies(bp);
+  for (int l = L - 2; l >= (fused ? 2 : lmin); --l) {
     launch_restrict3u(restrict_to(l), s);
     h->launches += 1;
   }
-  for (int l = lmin + 1; l <= L - 1; ++l) {
+  if (fused) {
+    launch_bottom3u(bp, s);
+    h->launches += 1;
+  }
+  for (int l = fused ? 4 : lmin + 1; l <= L - 1; ++l) {
     launch_prolong3u(prolong_to(l), s);
     h->launches += 1;
   }
