@@ -489,6 +489,7 @@ adafac_status run_setup(adafac_handle h, const double* eps_in, const double* f_i
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
       sw.nz = sweep3_default_nz(sw.nc, nsm);
       sw.nz_down = sweep3_default_nz_down(sw.nc, nsm);
+      sw.nz_downu = sweep3_default_nz_downu(sw.nc, nsm);
     }
     sw.a_c = (float)a.cst[13];
     sw.a_f = (float)a.cst[12];

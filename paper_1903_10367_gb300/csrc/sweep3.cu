@@ -268,6 +268,18 @@ __global__ void __launch_bounds__(NT, MINB)
   // DOWNU: the largest biased exponent of the u this thread writes (the
   // scale of the next refinement step's fixed-point residual)
   unsigned uexp_max = 0;
+  // DOWNU: the FP64 iterate at the thread's columns of an owned plane
+  double un[RB][2];
+  auto fetch_u = [&](int sp) {
+    const bool own = sp >= oz0 && sp < oz1 && sp >= 1 && sp <= n - 1;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      const long long urow = ((long long)sp * (n + 1) + y0 + i) * (n + 1);
+      un[i][0] = (own && myB[i] != 0.f && mxB.x != 0.f) ? p.u[urow + xb] : 0.0;
+      un[i][1] = (own && myB[i] != 0.f && mxB.y != 0.f) ? p.u[urow + xb + 1] : 0.0;
+    }
+  };
+  if (MODE == SWEEP_DOWNU) fetch_u(t0 - 1);
   auto expo = [](double v) {
     return (unsigned)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff);
   };
@@ -300,15 +312,16 @@ __global__ void __launch_bounds__(NT, MINB)
     const float* E = sE + rs0 * BOXW + 2 + 2 * pc;
     const float* Rh = sRhs + (rs0 + 1) * BOXW + 3 + 2 * pc;
     const float* qx = sQX + (s & 1) * NQX;
-    // DOWNU: fetch the FP64 iterate first (its latency overlaps the stencil)
+    // DOWNU: the FP64 iterate of plane s came in during the previous step;
+    // the loads of plane s + 1 go out now (their latency overlaps this step)
     double uo[RB][2];
-    if (MODE == SWEEP_DOWNU && doB) {
+    if (MODE == SWEEP_DOWNU) {
 #pragma unroll
       for (int i = 0; i < RB; ++i) {
-        const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
-        uo[i][0] = (myB[i] != 0.f && mxB.x != 0.f) ? p.u[urow + xb] : 0.0;
-        uo[i][1] = (myB[i] != 0.f && mxB.y != 0.f) ? p.u[urow + xb + 1] : 0.0;
+        uo[i][0] = un[i][0];
+        uo[i][1] = un[i][1];
       }
+      fetch_u(s + 1);
     }
     RowPair up = row_pair(E), ce = row_pair(E + BOXW);
 #pragma unroll
@@ -874,6 +887,9 @@ void sweep3_grid_down(int nc, int nz, dim3* grid) {
 }
 // threads and blocks per SM of the down-passes
 constexpr int kDownNT = 128, kDownMinB = 4;
+// the last down-pass holds the next plane's FP64 iterate in registers: three
+// blocks per SM
+constexpr int kDownUMinB = 3;
 
 int sweep3_default_nz(int nc, int nsm) {
   dim3 g;
@@ -887,6 +903,12 @@ int sweep3_default_nz_down(int nc, int nsm) {
   return std::min(std::max(1, (kDownMinB * nsm) / (int)(g.x * g.y)), std::max(1, 3 * nc - 1));
 }
 
+int sweep3_default_nz_downu(int nc, int nsm) {
+  dim3 g;
+  sweep3_grid_down(nc, 1, &g);
+  return std::min(std::max(1, (kDownUMinB * nsm) / (int)(g.x * g.y)), std::max(1, 3 * nc - 1));
+}
+
 bool sweep3_prepare() {
   return cudaFuncSetAttribute(k_up3<SWEEP_UP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)USMEM_BYTES) == cudaSuccess &&
@@ -895,7 +917,7 @@ bool sweep3_prepare() {
          cudaFuncSetAttribute(k_down3<SWEEP_DOWN, kDownNT, kDownMinB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SMEM_BYTES) == cudaSuccess &&
-         cudaFuncSetAttribute(k_down3<SWEEP_DOWNU, kDownNT, kDownMinB>,
+         cudaFuncSetAttribute(k_down3<SWEEP_DOWNU, kDownNT, kDownUMinB>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SMEM_BYTES) == cudaSuccess;
 }
@@ -904,7 +926,7 @@ void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int m
                    cudaStream_t s) {
   dim3 grid;
   if (mode == SWEEP_DOWN || mode == SWEEP_DOWNU)
-    sweep3_grid_down(p.nc, p.nz_down, &grid);
+    sweep3_grid_down(p.nc, mode == SWEEP_DOWNU ? p.nz_downu : p.nz_down, &grid);
   else
     sweep3_grid(p.nc, p.nz, &grid);
   switch (mode) {
@@ -919,7 +941,7 @@ void launch_sweep3(const Sweep3Params& p, const Sweep3Maps& maps, int ein, int m
           <<<grid, kDownNT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
       break;
     default:
-      k_down3<SWEEP_DOWNU, kDownNT, kDownMinB>
+      k_down3<SWEEP_DOWNU, kDownNT, kDownUMinB>
           <<<grid, kDownNT, SMEM_BYTES, s>>>(p, maps.e[ein], maps.rhs);
       break;
   }

@@ -25,6 +25,7 @@ struct Sweep3Params {
   int n = 0, nc = 0;               // fine cells, coarse cells
   int nz = 1;                      // up-passes: slabs of the interior coarse planes
   int nz_down = 1;                 // down-passes: slabs of the interior fine planes
+  int nz_downu = 1;                // the last down-pass of a refinement step: the same
   int ldx = 0;                     // row stride of the FP32 fine arrays (multiple of 4)
   // uniform stencil: A e = a_c e + a_f (6 faces) + a_e (12 edges) + a_k (8 corners)
   float a_c = 0, a_f = 0, a_e = 0, a_k = 0;
@@ -85,6 +86,7 @@ void sweep3_grid_down(int nc, int nz, dim3* grid);  // down-passes (64-column ti
 // default slab counts: as many as one wave of resident blocks on nsm SMs allows
 int sweep3_default_nz(int nc, int nsm);
 int sweep3_default_nz_down(int nc, int nsm);
+int sweep3_default_nz_downu(int nc, int nsm);
 int refine3_blocks(int n, int zc);
 // planes per block of the refinement residual (one wave of resident blocks)
 int refine3_zc(int n);
