@@ -35,6 +35,7 @@
 //     restriction and the damping right-hand side of their coarse columns as
 //     the planes pass.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "mbarrier.cuh"
@@ -485,6 +486,11 @@ __global__ void __launch_bounds__(UNT, kUpMinB)
     const int y = 3 * Jy0 - 2 + rc0 + i;
     myC[i] = (i < ncrows && y >= 1 && y <= n - 1) ? 1.f : 0.f;
   }
+  // the residual region reaches the boundary (rows or columns 0 or n and
+  // beyond) only in blocks at the end of a grid whose interior the tiles do
+  // not divide: only there does the residual need its masks
+  const bool edge = 3 * Jy0 - 2 < 1 || 3 * Jy0 - 2 + UCH - 1 > n - 1 || cstart < 1 ||
+                    cstart + 2 * UNACT - 1 > n - 1;
   const float2 ac2 = f2(p.a_c), ae2 = f2(p.a_e), ak2 = f2(p.a_k);
   const float2 neg1 = f2(-1.f);
   float2 PR[URC], YR[URC];
@@ -542,23 +548,30 @@ __global__ void __launch_bounds__(UNT, kUpMinB)
         const float* E = sE + rc0 * UBOXW + (c - 1 - xA);
         const float* Rh = sRhs + (rc0 + 1) * UBOXW + (c - xA);
         float* sRn = sR + (rn & 1) * USR_F;
-        RowPair up = row_pair(E), ce = row_pair(E + UBOXW);
+        // the same rows with and without the boundary masks (multiplying by
+        // 1 changes nothing, so both give the same values)
+        auto rows = [&](auto masked) {
+          RowPair up = row_pair(E), ce = row_pair(E + UBOXW);
 #pragma unroll
-        for (int i = 0; i < URC; ++i) {
-          if (i >= ncrows) break;
-          const RowPair dn = row_pair(E + (i + 2) * UBOXW);
-          const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
-          if (store) {
-            const float2 Ae = add2(PR[i], q.Y);
-            const float2 rhs = make_float2(Rh[i * UBOXW], Rh[i * UBOXW + 1]);
-            const float2 rho = mul2(fma2(Ae, neg1, rhs), mul2(mxC, f2(zm * myC[i])));
-            st2(sRn + (rc0 + i) * USR_P + 2 * pc, rho);
+          for (int i = 0; i < URC; ++i) {
+            if (i >= ncrows) break;
+            const RowPair dn = row_pair(E + (i + 2) * UBOXW);
+            const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+            if (store) {
+              const float2 Ae = add2(PR[i], q.Y);
+              const float2 rhs = make_float2(Rh[i * UBOXW], Rh[i * UBOXW + 1]);
+              float2 rho = fma2(Ae, neg1, rhs);
+              if constexpr (decltype(masked)::value) rho = mul2(rho, mul2(mxC, f2(zm * myC[i])));
+              st2(sRn + (rc0 + i) * USR_P + 2 * pc, rho);
+            }
+            PR[i] = add2(q.W, YR[i]);
+            YR[i] = q.Y;
+            up = ce;
+            ce = dn;
           }
-          PR[i] = add2(q.W, YR[i]);
-          YR[i] = q.Y;
-          up = ce;
-          ce = dn;
-        }
+        };
+        if (edge) rows(std::true_type());
+        else rows(std::false_type());
       }
       // sR column j = absolute column cstart + j, row j = residual row j
       wbase = sR + (r & 1) * USR_F + soff;
