@@ -26,14 +26,17 @@
 // stencil is split into an in-plane part W_p and an off-plane part Y_p per
 // plane, A e(s) = W_s + Y_{s-1} + Y_{s+1}; the partial sum W_s + Y_{s-1} and
 // Y_s roll along in registers.
-//   * Down-passes own 64 fine columns (the 32 lane pairs of a warp) and 24
-//     rows; they prolong q with the d-linear weights in three interpolation
-//     stages (z per plane, x per plane into shared memory, y per thread).
-//   * Up-passes own 41 x 4 coarse columns (their restriction targets; two
-//     x-tiles cover 82 coarse columns exactly), form rho on the owned box + 1
-//     (the support of the restriction) in shared memory, and accumulate the
+//   * Down-passes own 64 fine columns (the 32 lane pairs of a warp) and 22
+//     rows from row 1; they prolong q with the d-linear weights in three
+//     interpolation stages (z per plane, x per plane into shared memory, y
+//     per thread).
+//   * Up-passes own 20 x 8 interior coarse columns (their restriction
+//     targets; four x-tiles and ten y-tiles cover the 80 x 80 interior coarse
+//     columns of a 243-cell grid exactly), form rho on the owned box + 1 (the
+//     support of the restriction) in shared memory, and accumulate the
 //     restriction and the damping right-hand side of their coarse columns as
 //     the planes pass.
+//   * Both split their planes into balanced slabs along z (grid z).
 #include <algorithm>
 #include <type_traits>
 
