@@ -126,10 +126,11 @@ __device__ __forceinline__ Parts parts(const RowPair& up, const RowPair& ce, con
 }
 
 // ---- down-passes ----------------------------------------------------------------
-// A block owns 64 fine columns in x (all 32 lane pairs busy; no coarse
-// alignment is needed), OH rows and one of gridDim.z balanced slabs of the
-// interior planes 1 .. n - 1 (no coarse alignment is needed in z either).  NT threads are 32
-// column pairs x NT/32 row strips; MINB blocks per SM.
+// A block owns 64 fine columns in x from column 64 bx + 1 (all 32 lane pairs
+// busy; no coarse alignment is needed), OH rows from row OH by + 1 and one of
+// gridDim.z balanced slabs of the interior planes 1 .. n - 1 (no coarse
+// alignment is needed in z either).  NT threads are 32 column pairs x NT/32
+// row strips; MINB blocks per SM.
 template <int MODE, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_down3(const __grid_constant__ Sweep3Params p, const __grid_constant__ CUtensorMap tm_e,
@@ -154,7 +155,8 @@ __global__ void __launch_bounds__(NT, MINB)
   const int tid = threadIdx.x;
   const int pc = tid % NPAIR, strip = tid / NPAIR;
   const int Y0 = 1 + blockIdx.y * OH;                     // first owned row
-  const int xA = 64 * (int)blockIdx.x - 4, yA = Y0 - 1;     // staged box origin
+  const int xs = 64 * (int)blockIdx.x + 1;                // first owned column
+  const int xA = xs - 1, yA = Y0 - 1;                      // staged box origin
   const int oz0 = 1 + (int)((long long)blockIdx.z * (n - 1) / gridDim.z);  // owned planes
   const int oz1 = 1 + (int)((long long)(blockIdx.z + 1) * (n - 1) / gridDim.z);  // [oz0, oz1)
   // step t stages e plane t and rhs plane t-1 and updates plane s = t-1
@@ -178,11 +180,11 @@ __global__ void __launch_bounds__(NT, MINB)
   if (tid == 0)
     for (int t = t0; t < t0 + PREF && t < t1; ++t) issue(t);
 
-  // the pair (2 pc, 2 pc + 1) of the owned box is box columns 3 + 2 pc (+1);
+  // the pair (2 pc, 2 pc + 1) of the owned box is box columns 1 + 2 pc (+1);
   // the strip's owned rows rs0 + i (i < nr) are box rows rs0 + i + 1
   const int rs0 = strip * RBB + min(strip, RBX);
   const int nr = RBB + (strip < RBX ? 1 : 0);
-  const int xb = xA + 3 + 2 * pc;                          // odd
+  const int xb = xs + 2 * pc;                              // odd
   const float2 mxB = make_float2(xb >= 1 && xb <= n - 1 ? 1.f : 0.f,
                                  xb + 1 >= 1 && xb + 1 <= n - 1 ? 1.f : 0.f);
   const int y0 = Y0 + rs0;
@@ -201,9 +203,9 @@ __global__ void __launch_bounds__(NT, MINB)
   // prolongation of q: per plane the z-interpolated coarse window sQ (QW x QH,
   // origin (qx0, qy0)), then the x-interpolated values sQX at the owned
   // columns; each thread interpolates in y itself.  The owned columns x in
-  // [xA + 3, xA + 67) interpolate between coarse columns floor(x / 3) and + 1.
+  // [xs, xs + 64) interpolate between coarse columns floor(x / 3) and + 1.
   constexpr int NQ = (QW * QH + NT - 1) / NT, NX = NQX / NT;
-  const int qx0 = max(xA + 3, 0) / 3 - 1;
+  const int qx0 = xs / 3 - 1;
   int qoff[NQ];
   bool qok[NQ];
 #pragma unroll
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(NT, MINB)
   for (int k = 0; k < NX; ++k) {
     const int e = tid + k * NT;
     const int ky = e / 64, c = e % 64;
-    const int x = xA + 3 + c;
+    const int x = xs + c;
     const int Ox = min(max(x, 0) / 3, nc - 1);
     xq[k] = ky * QW + Ox - qx0;
     xt[k] = (float)(x - 3 * Ox) * (1.f / 3.f);
@@ -262,6 +264,9 @@ __global__ void __launch_bounds__(NT, MINB)
   __syncthreads();
   make_qx(mod3(t0 - 1), (t0 - 1) & 1);
 
+  // the block's columns and rows reach the boundary (or beyond): only then
+  // are its stores masked
+  const bool edge = xs + 63 > n - 1 || Y0 + OH - 1 > n - 1;
   const float2 ac2 = f2(p.a_c), ae2 = f2(p.a_e), ak2 = f2(p.a_k), w2 = f2(p.w_invd);
   const float2 neg1 = f2(-1.f);
   // rolling stencil parts per row: centre of the last plane, PR = W_s + Y_{s-1}
@@ -313,8 +318,8 @@ __global__ void __launch_bounds__(NT, MINB)
     const float* sRhs = sE + PLANE_F;
     const int s = t - 1;
     const bool doB = s >= oz0 && s < oz1 && s >= 1 && s <= n - 1;
-    const float* E = sE + rs0 * BOXW + 2 + 2 * pc;
-    const float* Rh = sRhs + (rs0 + 1) * BOXW + 3 + 2 * pc;
+    const float* E = sE + rs0 * BOXW + 2 * pc;
+    const float* Rh = sRhs + (rs0 + 1) * BOXW + 1 + 2 * pc;
     const float* qx = sQX + (s & 1) * NQX;
     // DOWNU: the FP64 iterate of plane s came in during the previous step;
     // the loads of plane s + 1 go out now (their latency overlaps this step)
@@ -327,45 +332,52 @@ __global__ void __launch_bounds__(NT, MINB)
       }
       fetch_u(s + 1);
     }
-    RowPair up = row_pair(E), ce = row_pair(E + BOXW);
-#pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      if (i >= nr) break;
-      const RowPair dn = row_pair(E + (i + 2) * BOXW);
-      const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
-      if (doB && myB[i] != 0.f) {
-        const float2 Ae = add2(PR[i], q.Y);
-        const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
-        const float2 rho = fma2(Ae, neg1, rhs);
-        const float2 q0 = ld2(qx + qrB[i]), q1 = ld2(qx + qrB[i] + 64);
-        const float2 pq = fma2(f2(tyB[i]), fma2(q0, neg1, q1), q0);
-        const float2 ek = add2(fma2(w2, rho, eR[i]), pq);
-        float* eo = p.e_out + s * fplane + (long long)(y0 + i) * ldx + xb;
-        if (MODE == SWEEP_DOWN) {
-          if (mxB.x != 0.f) eo[0] = ek.x;
-          if (mxB.y != 0.f) eo[1] = ek.y;
-        } else {
-          const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
-          if (mxB.x != 0.f) {
-            const double un = uo[i][0] + (double)ek.x;
-            p.u[urow + xb] = un;
-            uexp_max = max(uexp_max, expo(un));
-            eo[0] = 0.f;  // the zero buffer of the next refinement step
-          }
-          if (mxB.y != 0.f) {
-            const double un = uo[i][1] + (double)ek.y;
-            p.u[urow + xb + 1] = un;
-            uexp_max = max(uexp_max, expo(un));
-            eo[1] = 0.f;
+    // the same rows with and without the boundary masks: the down-pass
+    // blocks whose columns and rows are all interior store unconditionally
+    auto rows = [&](auto masked) {
+      constexpr bool M = decltype(masked)::value;
+      RowPair up = row_pair(E), ce = row_pair(E + BOXW);
+  #pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        if (i >= nr) break;
+        const RowPair dn = row_pair(E + (i + 2) * BOXW);
+        const Parts q = parts(up, ce, dn, ac2, ae2, ak2);
+        if (doB && (!M || myB[i] != 0.f)) {
+          const float2 Ae = add2(PR[i], q.Y);
+          const float2 rhs = make_float2(Rh[i * BOXW], Rh[i * BOXW + 1]);
+          const float2 rho = fma2(Ae, neg1, rhs);
+          const float2 q0 = ld2(qx + qrB[i]), q1 = ld2(qx + qrB[i] + 64);
+          const float2 pq = fma2(f2(tyB[i]), fma2(q0, neg1, q1), q0);
+          const float2 ek = add2(fma2(w2, rho, eR[i]), pq);
+          float* eo = p.e_out + s * fplane + (long long)(y0 + i) * ldx + xb;
+          if (MODE == SWEEP_DOWN) {
+            if (!M || mxB.x != 0.f) eo[0] = ek.x;
+            if (!M || mxB.y != 0.f) eo[1] = ek.y;
+          } else {
+            const long long urow = ((long long)s * (n + 1) + y0 + i) * (n + 1);
+            if (mxB.x != 0.f) {
+              const double un = uo[i][0] + (double)ek.x;
+              p.u[urow + xb] = un;
+              uexp_max = max(uexp_max, expo(un));
+              eo[0] = 0.f;  // the zero buffer of the next refinement step
+            }
+            if (mxB.y != 0.f) {
+              const double un = uo[i][1] + (double)ek.y;
+              p.u[urow + xb + 1] = un;
+              uexp_max = max(uexp_max, expo(un));
+              eo[1] = 0.f;
+            }
           }
         }
+        PR[i] = add2(q.W, YR[i]);
+        YR[i] = q.Y;
+        eR[i] = ce.c;
+        up = ce;
+        ce = dn;
       }
-      PR[i] = add2(q.W, YR[i]);
-      YR[i] = q.Y;
-      eR[i] = ce.c;
-      up = ce;
-      ce = dn;
-    }
+    };
+    if (MODE == SWEEP_DOWN && !edge) rows(std::false_type());
+    else rows(std::true_type());
     if (t + 1 < t1) {
       make_qx(mod3(s + 1), (s + 1) & 1);
       if (t + 2 < t1) make_q(s + 2, mod3(s + 2));
@@ -899,7 +911,7 @@ void sweep3_grid(int nc, int nz, dim3* grid) {
 
 void sweep3_grid_down(int nc, int nz, dim3* grid) {
   const int ni = std::max(1, 3 * nc - 1);  // interior fine rows and planes
-  *grid = dim3((3 * nc + 63) / 64, (ni + OH - 1) / OH, std::min(std::max(nz, 1), ni));
+  *grid = dim3((ni + 63) / 64, (ni + OH - 1) / OH, std::min(std::max(nz, 1), ni));
 }
 // threads and blocks per SM of the down-passes
 constexpr int kDownNT = 128, kDownMinB = 4;

@@ -12,9 +12,10 @@ namespace adafac {
 // DOWN: down-pass; DOWNU: last down-pass (u += e, the other buffer zeroed)
 enum SweepMode { SWEEP_UP = 0, SWEEP_UPE = 1, SWEEP_DOWN = 2, SWEEP_DOWNU = 3 };
 
-// down-passes: 64 fine columns x kDownRows rows per block (tiles from row 1:
-// eleven tiles cover the 242 interior rows of a 243-cell grid exactly), staged
-// box 68 x (kDownRows + 2) floats (x origin 64 bx - 4, a 16-byte boundary)
+// down-passes: 64 fine columns x kDownRows rows per block (tiles from column
+// and row 1: eleven tiles cover the 242 interior rows of a 243-cell grid
+// exactly), staged box 68 x (kDownRows + 2) floats (x origin 64 bx, a 16-byte
+// boundary)
 constexpr int kDownRows = 22;
 constexpr int kBoxW = 68, kBoxH = kDownRows + 2;
 // up-passes: 20 x 8 interior coarse columns per block, staged box 64 x 28 floats
