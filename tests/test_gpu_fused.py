@@ -82,8 +82,9 @@ def test_fused_step_at_depth5_matches_the_oracle_step_by_step(depth5_steps, k):
     # coarse columns (the restriction and damping windows of coarse columns
     # 20 and 21 straddle a seam) in 11 slabs along z, and its blocks skip the
     # boundary masks (their residual regions stay inside the interior); the
-    # down-pass has 4 x 11 tiles of 64 x 22 fine columns in 13 slabs.  Depths
-    # 2 to 4 take the masked up-pass.  One refinement step of k FP32 cycles
+    # down-pass has 4 x 11 tiles of 64 x 22 fine columns in 13 slabs, three
+    # of the four x-tiles storing without masks.  Depths 2 to 4 take the
+    # masked paths.  One refinement step of k FP32 cycles
     # from a random iterate must give the correction of k FP64 oracle cycles,
     # and the level vectors of the step's last cycle those of the oracle's
     # k-th cycle: r_l, b~_l = omega S~^T r_{l+1} and g_l = c_l - c~_l.
